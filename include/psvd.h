@@ -1,0 +1,188 @@
+/*
+ * psvd -- SVD of batched tall matrices through the polar decomposition,
+ * with a numerically stable (regularized) backward pass.  GB300 (sm_103a).
+ *
+ * The method ("Fast Differentiable SVD on GPU via Polar Decomposition"):
+ *   forward  (Algorithm 1): normalize M (Algorithm 2), compute the polar factor W
+ *            by odd-cubic polynomial iterations X <- X (c1 I + c3 X^T X) (CANS,
+ *            Appendix A.4 / B.8), H = (W^T M)_sym, EVD H = V Sigma V^T, U = W V,
+ *            QR of U if a column norm of U is off 1 by more than eps_qr
+ *            (Appendix A.2).
+ *   backward (Algorithm 4): the regularized polar + EVD pseudo-gradient,
+ *            evaluated from the cached factors only (no iterate is stored).
+ *
+ * Conventions for every entry point
+ *  - Matrices are row-major and batch-contiguous: element (b, i, j) of an
+ *    m x n batch lives at p[b*m*n + i*n + j].  m >= n >= 1, batch >= 1
+ *    (callers transpose wide matrices and swap U and V).
+ *  - Every pointer argument is a DEVICE pointer owned by the caller unless its
+ *    comment says otherwise; the library never frees or retains it.
+ *  - The library allocates no memory: every call takes a caller-owned device
+ *    workspace of at least psvd_*_workspace_bytes(...) bytes, 256-byte aligned.
+ *  - All work is enqueued on `stream` (a cudaStream_t passed as void*; NULL =
+ *    legacy default stream).  Unless stated otherwise calls are asynchronous: the
+ *    return value reports argument and launch errors only, per-matrix outcomes
+ *    land in the device-side psvd_info array.
+ *  - Calls on the same workspace must not overlap on the GPU.
+ */
+#ifndef PSVD_H
+#define PSVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PSVD_OK                 0
+#define PSVD_NOT_CONVERGED      1   /* iteration cap reached; outputs still written   */
+#define PSVD_ERR_ARG           -1   /* bad size, m < n, null required pointer, ...    */
+#define PSVD_ERR_WORKSPACE     -2   /* ws_bytes smaller than the query says           */
+#define PSVD_ERR_NONFINITE     -3   /* input had NaN/Inf; outputs are NaN-filled      */
+#define PSVD_ERR_CUDA          -4   /* a CUDA launch/runtime call failed               */
+#define PSVD_ERR_TIMEOUT       -5   /* a bounded device-side wait expired             */
+#define PSVD_ERR_UNSUPPORTED   -6   /* device is not sm_103 / sm_100 class            */
+
+/* ---- options ----------------------------------------------------------- */
+#define PSVD_PREC_FP32    0   /* every product FP32-accurate (split hi+lo TF32, "3xTF32") */
+#define PSVD_PREC_MIXED   1   /* BF16 early steps -> TF32 -> 3xTF32 polish, chosen from
+                                 the measured orthogonality residual                       */
+
+#define PSVD_SCHED_CANS     0 /* conservative CANS: preprocessing for [t,1] then greedy
+                                 optimal cubics from [1-delta, 1+delta] (Appendix B.8)     */
+#define PSVD_SCHED_LEARNED  1 /* greedy optimal cubics from [l_b, 1], l_b a predicted lower
+                                 bound of sigma_min(X0) per matrix (opts.lower_bound)       */
+#define PSVD_SCHED_NS       2 /* classical Newton-Schulz, p(x) = 1.5 x - 0.5 x^3           */
+
+typedef struct psvd_opts {
+    int    precision;     /* PSVD_PREC_*                                        default 0    */
+    int    schedule;      /* PSVD_SCHED_*                                       default 0    */
+    double delta;         /* CANS delta (Appendix B.8)                          default 0.99 */
+    int    pre_iters;     /* CANS preprocessing steps                           default 2    */
+    int    max_iter;      /* cap on main polynomial steps (Appendix A.4)        default 50   */
+    double tol;           /* stop when ||X^T X - I||_F / sqrt(n) <= tol         default 1e-5 */
+    double eps_qr;        /* QR fallback threshold on | ||U_i|| - 1 |           default 1e-5 */
+    const float *lower_bound; /* DEVICE [batch]: schedule 1's lower bounds (NULL otherwise) */
+    int    budget;        /* schedule 1: steps allowed before the conservative rerun
+                             (0 = automatic: predicted steps + 3)                           */
+} psvd_opts;
+
+/* Fills *o with the defaults above (host pointer). */
+void psvd_default_opts(psvd_opts *o);
+
+/* Per-matrix outcome, written to a DEVICE array of `batch` records. */
+typedef struct psvd_info {
+    int   status;          /* PSVD_OK, PSVD_NOT_CONVERGED or PSVD_ERR_NONFINITE         */
+    int   iters;           /* polynomial steps applied                                  */
+    int   qr_fallback;     /* 1 if U was re-orthogonalized by QR (Algorithm 1 step 8)    */
+    int   sched_fallback;  /* 1 if the learned schedule missed tol and the conservative
+                              schedule was rerun                                          */
+    int   steps_bf16;      /* steps taken in each precision (mixed path)                 */
+    int   steps_tf32;
+    int   steps_3xtf32;
+    float ortho_resid;     /* final ||W^T W - I||_F / sqrt(n)                            */
+    float scale;           /* sqrt(||M||_1 ||M||_inf) of Algorithm 2                     */
+} psvd_info;
+
+/* ---- workspace queries ---------------------------------------------------- */
+size_t psvd_polar_workspace_bytes(int64_t batch, int64_t m, int64_t n, const psvd_opts *opts);
+size_t psvd_svd_workspace_bytes(int64_t batch, int64_t m, int64_t n, const psvd_opts *opts);
+size_t psvd_svd_bwd_workspace_bytes(int64_t batch, int64_t m, int64_t n);
+size_t psvd_polar_bwd_workspace_bytes(int64_t batch, int64_t m, int64_t n);
+size_t psvd_eigh_workspace_bytes(int64_t batch, int64_t n);
+
+/* ---- forward ----------------------------------------------------------------
+ * psvd_polar_fwd -- right polar decomposition M = W H (Definition 2.1) by
+ *   Algorithm 1 steps 1-4: W (m x n, W^T W = I) and H = (W^T M)_sym (n x n, FP64
+ *   symmetrization, stored FP32).  A: batch x m x n input (read only).
+ *   W: batch x m x n out.  H: batch x n x n out (may be NULL).  info: batch records.
+ */
+int psvd_polar_fwd(const float *A, float *W, float *H, int64_t batch, int64_t m, int64_t n,
+                   const psvd_opts *opts, void *ws, size_t ws_bytes, psvd_info *info,
+                   void *stream);
+
+/* psvd_svd_fwd -- thin SVD M = U Sigma V^T by Algorithm 1.
+ *   U: batch x m x n, S: batch x n (descending, >= 0 up to rounding), VT: batch x n x n
+ *   (rows are right singular vectors; each V column's largest-|.| entry is positive).
+ *   This call synchronizes `stream` once (it reads back the QR-fallback flags). */
+int psvd_svd_fwd(const float *A, float *U, float *S, float *VT, int64_t batch, int64_t m,
+                 int64_t n, const psvd_opts *opts, void *ws, size_t ws_bytes,
+                 psvd_info *info, void *stream);
+
+/* psvd_eigh -- symmetric EVD H = V diag(S) V^T (Algorithm 1 step 5) of a batch of
+ *   n x n symmetric matrices (only the upper triangle is read).  S descending,
+ *   VT rows = eigenvectors with the sign convention above. */
+int psvd_eigh(const float *Hs, float *S, float *VT, int64_t batch, int64_t n,
+              void *ws, size_t ws_bytes, void *stream);
+
+/* ---- backward ----------------------------------------------------------------
+ * psvd_svd_bwd -- Algorithm 4's backward pass from the cached factors:
+ *   W = U V^T, Wbar = Ubar V^T, Vbar_tot = Vbar + W^T Ubar,
+ *   B = (V^T Vbar_tot - Vbar_tot^T V)/2, Hbar = V (diag(Sbar) + K_eps^T o B) V^T,
+ *   R_eps = V Sigma (Sigma^2 + eps^(1/2))^-1 V^T, C = (Hbar - R_eps M^T Wbar R_eps)_sym,
+ *   X = V (T_eps o V^T C V) V^T, Mbar = Wbar R_eps + 2 M X.
+ *   dU / dS / dVT are the incoming gradients of U, S and V^T; any may be NULL (zero).
+ *   kreg_mode selects K_eps: 0 = (s_i-s_j)/((s_i-s_j)^2 + eps^(1/2)) as in Algorithm 4,
+ *   1 = (s_i-s_j)/((s_i-s_j)^2 + eps^2) as in Section 5.2, 2 = exact 1/(s_i-s_j) with
+ *   ties (|s_i-s_j| <= 1e-6 s_max) masked and eps = 0 in R and T.
+ *   dA: batch x m x n out. */
+int psvd_svd_bwd(const float *A, const float *U, const float *S, const float *VT,
+                 const float *dU, const float *dS, const float *dVT, float *dA,
+                 int64_t batch, int64_t m, int64_t n, double eps, int kreg_mode,
+                 void *ws, size_t ws_bytes, void *stream);
+
+/* psvd_polar_bwd -- Algorithm 3 (Proposition 3.2): from M, W, H and the incoming
+ *   gradients dW (m x n, may be NULL) and dH (n x n, may be NULL; its symmetric part
+ *   is used), computes the EVD of H and
+ *   Mbar = Wbar H_eps^-1 + 2 M V (T_eps o V^T B V) V^T with
+ *   B = (Hbar - H_eps^-1 M^T Wbar H_eps^-1)_sym.  eps = 0 gives Theorem 3.1. */
+int psvd_polar_bwd(const float *A, const float *W, const float *H, const float *dW,
+                   const float *dH, float *dA, int64_t batch, int64_t m, int64_t n,
+                   double eps, void *ws, size_t ws_bytes, void *stream);
+
+/* ---- learned schedule (the lower-bound predictor) ---------------------------
+ * psvd_sketch_features -- 8 features per matrix of X0 = M / sqrt(||M||_1 ||M||_inf):
+ *   Hutchinson estimates of tr(G^k)/n, k = 1..4 (G = X0^T X0) with the caller's
+ *   Rademacher probes Z (DEVICE, batch x n x s, entries +-1), log(||X0||_F^2 / n),
+ *   log(f4/f3), log(n)/10, log(m/n).  F: batch x 8 out.  ws as for svd_bwd. */
+int psvd_sketch_features(const float *A, const float *Z, int64_t s, float *F, int64_t batch,
+                         int64_t m, int64_t n, void *ws, size_t ws_bytes, void *stream);
+size_t psvd_sketch_workspace_bytes(int64_t batch, int64_t m, int64_t n, int64_t s);
+
+/* psvd_mlp_fwd -- y = W3 relu(W2 relu(W1 f + b1) + b2) + b3 for F (nb x 8); params is
+ *   one DEVICE float array [W1 64x8 | b1 64 | W2 64x64 | b2 64 | W3 1x64 | b3 1]
+ *   (PSVD_MLP_NPARAMS floats).  Y: nb out. */
+#define PSVD_MLP_NPARAMS (64 * 8 + 64 + 64 * 64 + 64 + 64 + 1)
+int psvd_mlp_fwd(const float *params, const float *F, float *Y, int64_t nb, void *stream);
+
+/* psvd_mlp_train_step -- one Adam step on 0.5 mean (y - target)^2 over the batch.
+ *   grads (PSVD_MLP_NPARAMS floats), m1/m2 (Adam moments, same size) are DEVICE
+ *   buffers; `step` is the 1-based Adam step count.  loss: DEVICE float out (may be NULL). */
+int psvd_mlp_train_step(float *params, float *grads, float *m1, float *m2, const float *F,
+                        const float *target, int64_t nb, float lr, int step, float *loss,
+                        void *stream);
+/* psvd_mlp_grad -- loss and gradients only (no parameter update). */
+int psvd_mlp_grad(const float *params, const float *F, const float *target, int64_t nb,
+                  float *grads, float *loss, void *stream);
+
+/* ---- building block ------------------------------------------------------------
+ * psvd_gemm_tn -- D[b] = A[b] B[b]^T for A: batch x M x K, B: batch x N x K, D: batch x M x N
+ *   (all row-major, contiguous) on the tcgen05 tensor cores; the single product kernel
+ *   behind every matrix multiplication of Algorithms 1 and 4 (Gram X^T X, X p(X^T X),
+ *   W^T M, W V and the backward chain).  precision: 0 = BF16 operands, 1 = TF32
+ *   operands, 2 = split hi+lo TF32 (FP32-accurate).  FP32 accumulation. */
+size_t psvd_gemm_workspace_bytes(int64_t batch, int64_t M, int64_t N, int64_t K);
+int psvd_gemm_tn(const float *A, const float *B, float *D, int64_t batch, int64_t M, int64_t N,
+                 int64_t K, int precision, void *ws, size_t ws_bytes, void *stream);
+
+/* ---- misc ------------------------------------------------------------------ */
+const char *psvd_status_string(int status);
+/* Number of kernels this library has launched in the calling process (all threads). */
+uint64_t psvd_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSVD_H */

@@ -1,0 +1,541 @@
+// Polar factor W of M (Definition 2.1) by the matmul-only polynomial iteration of
+// Algorithm 1 (steps 1-4):
+//   X0 = M / sqrt(||M||_1 ||M||_inf)                          (Algorithm 2)
+//   step k:  G_k = X_k^T X_k,  r_k = ||G_k - I||_F / sqrt(n)   (stop if r_k <= tol)
+//            P_k = c1_k I + c3_k G_k,  X_{k+1} = X_k P_k         (degree-3 CANS / NS step)
+//   H = (W^T M)_sym with W = X_final                           (FP64 averaging)
+// Each step is three launches: the Gram product (upper-triangle tiles, with the
+// polynomial and the residual fused in its epilogue), a per-matrix decision
+// kernel (stop / precision of the next step), and the apply product X_k P_k
+// whose epilogue writes X_{k+1} both row-major and transposed in the precision
+// the next step uses.  Matrices that finished are skipped by every later CTA.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "polar.cuh"
+#include "schedule.h"
+
+namespace psvd {
+
+// ------------------------------------------------------------ Algorithm 2
+__global__ void norm_panel_kernel(const float *__restrict__ A, int m, int n, float *rowsum, float *colsum,
+                                  int *nonfinite) {
+    __shared__ float sh[8][33];
+    const int b = blockIdx.z;
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    const int r0 = blockIdx.y * 256;
+    const float *Ab = A + (long long)b * m * n;
+    float cs = 0.f;
+    bool bad = false;
+    for (int i = threadIdx.y; i < 256; i += 8) {
+        const int r = r0 + i;
+        if (r >= m) break;                       // uniform within the warp (one row per warp)
+        const float x = c < n ? Ab[(long long)r * n + c] : 0.f;
+        bad |= !isfinite(x);
+        const float ax = fabsf(x);
+        cs += ax;
+        const float rs = warp_sum(ax);
+        if (threadIdx.x == 0) atomicAdd(&rowsum[(long long)b * m + r], rs);
+    }
+    sh[threadIdx.y][threadIdx.x] = cs;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < n) {
+        float t = 0.f;
+        for (int y = 0; y < 8; ++y) t += sh[y][threadIdx.x];
+        atomicAdd(&colsum[(long long)b * n + c], t);
+    }
+    if (bad) nonfinite[b] = 1;
+}
+
+// One block per matrix: s = sqrt(max col l1 * max row l1); special cases set the
+// matrix done (zero matrix: W = 0 and the QR step supplies U; non-finite input).
+__global__ void norm_finalize_kernel(const float *rowsum, const float *colsum, const int *nonfinite, int m, int n,
+                                     float *scale, int *done, int *status, int *fin) {
+    __shared__ float sm[32];
+    const int b = blockIdx.x;
+    float r = 0.f, c = 0.f;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) r = fmaxf(r, rowsum[(long long)b * m + i]);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) c = fmaxf(c, colsum[(long long)b * n + j]);
+    r = warp_max(r);
+    c = warp_max(c);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0) { sm[w] = r; sm[16 + w] = c; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < nw; ++i) { r = fmaxf(r, sm[i]); c = fmaxf(c, sm[16 + i]); }
+        r = fmaxf(r, sm[0]);
+        c = fmaxf(c, sm[16]);
+        const double s = sqrt((double)r * (double)c);
+        scale[b] = (float)s;
+        if (nonfinite[b]) { done[b] = 1; status[b] = PSVD_ERR_NONFINITE; fin[b] = 0; }
+        else if (s == 0.0) { done[b] = 1; status[b] = PSVD_OK; fin[b] = 0; }
+    }
+}
+
+__global__ void polar_init_kernel(int B, int prec0, int *done, int *fin, int *status, int *prec, int *steps,
+                                  int *fallback) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    done[b] = 0; fin[b] = 0; status[b] = PSVD_OK; fallback[b] = 0;
+    prec[b] = prec0;
+    steps[b] = steps[B + b] = steps[2 * B + b] = 0;
+}
+
+// ------------------------------------------------------------ schedules
+struct CoefTable {
+    int len;
+    float c1[72], c3[72];
+};
+
+// coef[(k * B + b) * 2 + {0,1}] for k < K.  Learned: greedy optimal cubics from
+// [l_b, 1] per matrix (FP64), and the step budget before the conservative rerun.
+__global__ void schedule_fill_kernel(int B, int K, CoefTable tab, const float *lower, int learned, double tol,
+                                     int budget_opt, const int *active, float *coef, int *budget) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    if (active && !active[b]) return;
+    if (!learned) {
+        for (int k = 0; k < K; ++k) {
+            const int i = k < tab.len ? k : tab.len - 1;
+            coef[((long long)k * B + b) * 2 + 0] = tab.c1[i];
+            coef[((long long)k * B + b) * 2 + 1] = tab.c3[i];
+        }
+        budget[b] = K;
+        return;
+    }
+    double l = (double)lower[b];
+    if (!(l > 1e-12)) l = 1e-12;
+    if (l > 0.999) l = 0.999;
+    double lo = l, hi = 1.0;
+    for (int k = 0; k < K; ++k) {
+        Cubic c = cans_cubic(lo, hi);
+        coef[((long long)k * B + b) * 2 + 0] = (float)c.c1;
+        coef[((long long)k * B + b) * 2 + 1] = (float)c.c3;
+        lo = 1.0 - c.e;
+        hi = 1.0 + c.e;
+    }
+    budget[b] = budget_opt > 0 ? budget_opt : greedy_steps_to(l, 0.5 * tol, K) + 3;
+}
+
+// ------------------------------------------------------------ step epilogues
+PSVD_DEV void store_prec(int p, long long o, float x, __nv_bfloat16 *p16, float *phi, float *plo) {
+    if (p == PREC_BF16) p16[o] = __float2bfloat16_rn(x);
+    else if (p == PREC_TF32) phi[o] = tf32_round(x);
+    else { float h, l; split_tf32(x, h, l); phi[o] = h; plo[o] = l; }
+}
+
+// Gram tile G = X^T X (upper tiles only): accumulates ||G - I||_F^2 and stores
+// P = c1 I + c3 G (and its mirror) in the precision of this step's apply.
+struct EpiGram {
+    int n, B;
+    const float *coef;   // coef + k*B*2
+    const int *prec;     // prec + k*B
+    double *res;         // res + k*B
+    __nv_bfloat16 *P16;
+    float *Phi, *Plo;
+    long long ldp;
+    struct Acc { double r; };
+    PSVD_DEV void begin(Acc &a) const { a.r = 0.0; }
+    PSVD_DEV void chunk(Acc &a, int b, int r, int c0, int ti, int tj, float (&v)[16]) const {
+        if (r >= n) return;
+        const int p = prec[b];
+        const float c1 = coef[2 * b], c3 = coef[2 * b + 1];
+        const double w = ti == tj ? 1.0 : 2.0;
+        const long long base = (long long)b * n * ldp;
+        double acc = 0.0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int c = c0 + i;
+            if (c >= n) break;
+            const float g = v[i];
+            const float d = g - (r == c ? 1.f : 0.f);
+            acc += (double)d * d;
+            const float pv = c3 * g + (r == c ? c1 : 0.f);
+            store_prec(p, base + (long long)r * ldp + c, pv, P16, Phi, Plo);
+            if (ti != tj) store_prec(p, base + (long long)c * ldp + r, pv, P16, Phi, Plo);
+        }
+        a.r += w * acc;
+    }
+    PSVD_DEV void finish(Acc &a, int b, int, int) const {
+        const double s = warp_sum(a.r);
+        if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(&res[b], s);
+    }
+};
+
+// X_{k+1} = X_k P_k: stored row-major and transposed in the next step's precision.
+struct EpiApply {
+    int m, n, B;
+    const int *prec_next;   // prec + (k+1)*B
+    __nv_bfloat16 *X16, *XT16;
+    float *Xhi, *Xlo, *XThi, *XTlo;
+    long long ldn, ldm;
+    struct Acc {};
+    PSVD_DEV void begin(Acc &) const {}
+    PSVD_DEV void chunk(Acc &, int b, int r, int c0, int, int, float (&v)[16]) const {
+        if (r >= m) return;
+        const int p = prec_next[b];
+        const long long rb = (long long)b * m * ldn + (long long)r * ldn;
+        const long long tb = (long long)b * n * ldm + r;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int c = c0 + i;
+            if (c >= n) break;
+            store_prec(p, rb + c, v[i], X16, Xhi, Xlo);
+            store_prec(p, tb + (long long)c * ldm, v[i], XT16, XThi, XTlo);
+        }
+    }
+    PSVD_DEV void finish(Acc &, int, int, int) const {}
+};
+
+// Per-matrix decision after the Gram of step k.
+__global__ void decide_kernel(int k, int B, int n, double tol, int mixed, int learned, int kcap, int *done,
+                              int *fin, int *status, int *prec, int *steps, const double *res, float *fres,
+                              const int *budget, int *fallback, int *notdone) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B || done[b]) return;
+    const double r = sqrt(res[(long long)k * B + b] / (double)n);
+    const int pk = prec[(long long)k * B + b];
+    if (!(r <= 1e30)) {                              // NaN / overflow in the iteration
+        done[b] = 1; fin[b] = k; status[b] = PSVD_NOT_CONVERGED; fres[b] = (float)r;
+        return;
+    }
+    if (r <= tol) { done[b] = 1; fin[b] = k; status[b] = PSVD_OK; fres[b] = (float)r; return; }
+    if (k >= kcap) { done[b] = 1; fin[b] = k; status[b] = PSVD_NOT_CONVERGED; fres[b] = (float)r; return; }
+    if (learned && k >= budget[b]) {
+        done[b] = 1; fin[b] = k; status[b] = PSVD_NOT_CONVERGED; fres[b] = (float)r; fallback[b] = 1;
+        return;
+    }
+    int pn = PREC_TF32X3;
+    if (mixed) {
+        const int want = r > kTauBF16 ? PREC_BF16 : (r > kTauTF32 ? PREC_TF32 : PREC_TF32X3);
+        pn = want > pk ? want : pk;
+    }
+    prec[(long long)(k + 1) * B + b] = pn;
+    steps[pk * B + b] += 1;
+    atomicAdd(&notdone[k], 1);
+}
+
+// W (user layout) from X_fin; leaves W split row-major in Xhi[0]/Xlo[0] and
+// transposed in XThi[0]/XTlo[0] for the products that follow (H, U).
+__global__ void polar_finalize_kernel(int m, int n, int B, const int *fin, const int *prec, const int *status,
+                                      PolarWS ws, float *W) {
+    __shared__ float tile[32][33];
+    const int b = blockIdx.z;
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const int f = fin[b];
+    const int par = f & 1;
+    const int p = prec[(long long)f * B + b];
+    const bool nan_out = status[b] == PSVD_ERR_NONFINITE;
+    const bool copy = par != 0 || p != PREC_TF32X3 || nan_out;
+    const long long rbase = (long long)b * m * ws.ldn;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        float x = 0.f;
+        if (r < m && c < n) {
+            const long long o = rbase + (long long)r * ws.ldn + c;
+            if (nan_out) x = __int_as_float(0x7fc00000);
+            else if (p == PREC_BF16) x = __bfloat162float(ws.X16[par][o]);
+            else if (p == PREC_TF32) x = ws.Xhi[par][o];
+            else x = ws.Xhi[par][o] + ws.Xlo[par][o];
+            if (W) W[(long long)b * m * n + (long long)r * n + c] = x;
+            if (copy) { float h, l; split_tf32(x, h, l); ws.Xhi[0][o] = h; ws.Xlo[0][o] = l; }
+        }
+        tile[i][threadIdx.x] = x;
+    }
+    if (!copy) return;                     // uniform per block
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (c < n && r < m) {
+            float h, l;
+            split_tf32(tile[threadIdx.x][i], h, l);
+            const long long o = (long long)b * n * ws.ldm + (long long)c * ws.ldm + r;
+            ws.XThi[0][o] = h;
+            ws.XTlo[0][o] = l;
+        }
+    }
+}
+
+// H = (Hraw + Hraw^T) / 2 in FP64, stored FP32 (Hsym, and H_out when given).
+__global__ void symmetrize_kernel(const float *Hraw, int n, float *Hsym, float *Hout) {
+    const int b = blockIdx.z;
+    const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
+    if (i >= n || j >= n) return;
+    const float *h = Hraw + (long long)b * n * n;
+    const double v = 0.5 * ((double)h[(long long)i * n + j] + (double)h[(long long)j * n + i]);
+    const long long o = (long long)b * n * n + (long long)i * n + j;
+    Hsym[o] = (float)v;
+    if (Hout) Hout[o] = (float)v;
+}
+
+__global__ void polar_info_kernel(int B, const int *status, const int *fin, const int *steps, const int *fallback,
+                                  const float *fres, const float *scale, psvd_info *info) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    psvd_info r;
+    r.status = status[b];
+    r.iters = steps[b] + steps[B + b] + steps[2 * B + b];
+    r.qr_fallback = 0;
+    r.sched_fallback = fallback[b];
+    r.steps_bf16 = steps[b];
+    r.steps_tf32 = steps[B + b];
+    r.steps_3xtf32 = steps[2 * B + b];
+    r.ortho_resid = fres[b];
+    r.scale = scale[b];
+    info[b] = r;
+}
+
+// ------------------------------------------------------------ host driver
+static int launch_step(PolarWS &w, int k, bool apply, double tol, bool learned, float *fres, cudaStream_t st) {
+    const int B = w.B, m = w.m, n = w.n;
+    const int par = k & 1, npar = (k + 1) & 1;
+    // Gram: A = B = X^T (n x m, K = m), upper-triangle tiles
+    {
+        MatView v16 = w.mixed ? view_of16(w.XT16[par], n, m, w.ldm, (long long)n * w.ldm, B) : MatView();
+        MatView vhi = view_of(w.XThi[par], n, m, w.ldm, (long long)n * w.ldm, B);
+        MatView vlo = view_of(w.XTlo[par], n, m, w.ldm, (long long)n * w.ldm, B);
+        GemmShape s;
+        memset(&s, 0, sizeof(s));
+        s.M = n; s.N = n; s.K = m; s.sym = 1;
+        s.prec = w.prec + (long long)k * B;
+        s.skip = w.done;
+        s.err = w.err;
+        EpiGram e;
+        e.n = n; e.B = B;
+        e.coef = w.coef + (long long)k * B * 2;
+        e.prec = w.prec + (long long)k * B;
+        e.res = w.res + (long long)k * B;
+        e.P16 = w.P16; e.Phi = w.Phi; e.Plo = w.Plo; e.ldp = w.ldn;
+        cudaError_t er = launch_gemm(w.mixed ? &v16 : nullptr, w.mixed ? &v16 : nullptr, &vhi, &vlo, &vhi, &vlo, s,
+                                     B, e, st);
+        if (er != cudaSuccess) return PSVD_ERR_CUDA;
+    }
+    decide_kernel<<<(B + 127) / 128, 128, 0, st>>>(k, B, n, tol, w.mixed ? 1 : 0, learned ? 1 : 0, w.kcap, w.done,
+                                                    w.fin, w.status, w.prec, w.steps, w.res, fres, w.budget,
+                                                    w.fallback, w.notdone);
+    count_launch(1);
+    if (cudaGetLastError() != cudaSuccess) return PSVD_ERR_CUDA;
+    if (!apply) return PSVD_OK;
+    // Apply: A = X (m x n, K = n), B = P (n x n, symmetric)
+    {
+        MatView a16 = w.mixed ? view_of16(w.X16[par], m, n, w.ldn, (long long)m * w.ldn, B) : MatView();
+        MatView ahi = view_of(w.Xhi[par], m, n, w.ldn, (long long)m * w.ldn, B);
+        MatView alo = view_of(w.Xlo[par], m, n, w.ldn, (long long)m * w.ldn, B);
+        MatView b16 = w.mixed ? view_of16(w.P16, n, n, w.ldn, (long long)n * w.ldn, B) : MatView();
+        MatView bhi = view_of(w.Phi, n, n, w.ldn, (long long)n * w.ldn, B);
+        MatView blo = view_of(w.Plo, n, n, w.ldn, (long long)n * w.ldn, B);
+        GemmShape s;
+        memset(&s, 0, sizeof(s));
+        s.M = m; s.N = n; s.K = n;
+        s.prec = w.prec + (long long)k * B;
+        s.skip = w.done;
+        s.err = w.err;
+        EpiApply e;
+        e.m = m; e.n = n; e.B = B;
+        e.prec_next = w.prec + (long long)(k + 1) * B;
+        e.X16 = w.X16[npar]; e.XT16 = w.XT16[npar];
+        e.Xhi = w.Xhi[npar]; e.Xlo = w.Xlo[npar]; e.XThi = w.XThi[npar]; e.XTlo = w.XTlo[npar];
+        e.ldn = w.ldn; e.ldm = w.ldm;
+        cudaError_t er = launch_gemm(w.mixed ? &a16 : nullptr, w.mixed ? &b16 : nullptr, &ahi, &alo, &bhi, &blo, s,
+                                     B, e, st);
+        if (er != cudaSuccess) return PSVD_ERR_CUDA;
+    }
+    return PSVD_OK;
+}
+
+static int read_int(const int *dptr, cudaStream_t st, int *out) {
+    if (cudaMemcpyAsync(out, dptr, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return PSVD_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return PSVD_ERR_CUDA;
+    return PSVD_OK;
+}
+
+// Runs steps 0..kcap until every matrix is done; `predicted` steps are launched
+// before the first host check, then 3 at a time.
+static int run_iteration(PolarWS &w, int predicted, double tol, bool learned, float *fres, cudaStream_t st) {
+    int k = 0;
+    int until = std::min(w.kcap, std::max(1, predicted));
+    while (true) {
+        for (; k <= until; ++k) {
+            int rc = launch_step(w, k, k < w.kcap, tol, learned, fres, st);
+            if (rc) return rc;
+        }
+        if (k > w.kcap) break;
+        int nd = 0;
+        if (int rc = read_int(w.notdone + (k - 1), st, &nd)) return rc;
+        if (nd == 0) break;
+        until = std::min(w.kcap, k + 2);
+    }
+    return PSVD_OK;
+}
+
+// Predicted number of steps for the conservative schedule to reach width tol/2
+// for spectra in [t, 1] (used only to size the first launch batch).
+static int predict_steps(const std::vector<Cubic> &sched, double tol) {
+    for (size_t k = 0; k < sched.size(); ++k)
+        if (sched[k].e <= 0.5 * tol) return (int)k + 1;
+    return (int)sched.size();
+}
+
+__global__ void fallback_reset_kernel(int B, int prec0, const int *fallback, int *done, int *prec, int *count) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    if (fallback[b]) { done[b] = 0; prec[b] = prec0; atomicAdd(count, 1); }
+    else done[b] = 1;
+}
+
+// restores done[] = 1 for every matrix after a rerun pass (all are final now)
+__global__ void set_all_done_kernel(int B, int *done) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) done[b] = 1;
+}
+
+static int prepare_x0(const float *A, PolarWS &w, cudaStream_t st, const int *skip) {
+    const int B = w.B, m = w.m, n = w.n;
+    SplitOut r, t;
+    r.ld = w.ldn; r.bstride = (long long)m * w.ldn;
+    t.ld = w.ldm; t.bstride = (long long)n * w.ldm;
+    if (w.mixed) { r.h16 = w.X16[0]; t.h16 = w.XT16[0]; }
+    else { r.hi = w.Xhi[0]; r.lo = w.Xlo[0]; t.hi = w.XThi[0]; t.lo = w.XTlo[0]; }
+    if (prepare_operand(A, n, (long long)m * n, B, m, n, false, 1.f, w.scale, r, st, skip) ||
+        prepare_operand(A, n, (long long)m * n, B, m, n, true, 1.f, w.scale, t, st, skip))
+        return PSVD_ERR_CUDA;
+    return PSVD_OK;
+}
+
+int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &w, const psvd_opts &o,
+                  psvd_info *info, cudaStream_t st) {
+    const int B = w.B, m = w.m, n = w.n;
+    const bool learned = o.schedule == PSVD_SCHED_LEARNED;
+    if (cudaMemsetAsync(w.rowsum, 0, sizeof(float) * (size_t)B * m, st) ||
+        cudaMemsetAsync(w.colsum, 0, sizeof(float) * (size_t)B * n, st) ||
+        cudaMemsetAsync(w.nonfinite, 0, sizeof(int) * (size_t)B, st) ||
+        cudaMemsetAsync(w.res, 0, sizeof(double) * (size_t)(w.kcap + 2) * B, st) ||
+        cudaMemsetAsync(w.notdone, 0, sizeof(int) * (size_t)(w.kcap + 2), st) ||
+        cudaMemsetAsync(w.fres, 0, sizeof(float) * (size_t)B, st) ||
+        cudaMemsetAsync(w.misc, 0, sizeof(int) * 8, st) ||
+        cudaMemsetAsync(w.err, 0, sizeof(unsigned) * 4, st))
+        return PSVD_ERR_CUDA;
+    const int prec0 = w.mixed ? PREC_BF16 : PREC_TF32X3;
+    polar_init_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, prec0, w.done, w.fin, w.status, w.prec, w.steps,
+                                                        w.fallback);
+    {
+        dim3 g((n + 31) / 32, (m + 255) / 256, B), blk(32, 8);
+        norm_panel_kernel<<<g, blk, 0, st>>>(A, m, n, w.rowsum, w.colsum, w.nonfinite);
+    }
+    norm_finalize_kernel<<<B, 256, 0, st>>>(w.rowsum, w.colsum, w.nonfinite, m, n, w.scale, w.done, w.status,
+                                            w.fin);
+    count_launch(3);
+    // coefficient tables: conservative CANS (Appendix B.8), classical NS, or learned bounds
+    CoefTable tab;
+    memset(&tab, 0, sizeof(tab));
+    std::vector<Cubic> cons = cans_schedule(o.delta, o.pre_iters, std::min(w.kcap + 1, 72));
+    std::vector<Cubic> sched = o.schedule == PSVD_SCHED_NS ? std::vector<Cubic>(1, Cubic{1.5, -0.5, 0.0}) : cons;
+    tab.len = (int)sched.size();
+    for (int i = 0; i < tab.len; ++i) { tab.c1[i] = (float)sched[i].c1; tab.c3[i] = (float)sched[i].c3; }
+    schedule_fill_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, w.kcap + 1, tab, o.lower_bound, learned ? 1 : 0,
+                                                          o.tol, o.budget, nullptr, w.coef, w.budget);
+    count_launch(1);
+    if (int rc = prepare_x0(A, w, st, w.done)) return rc;
+    if (want_h) {
+        SplitOut at;
+        at.hi = w.AThi; at.lo = w.ATlo; at.ld = w.ldm; at.bstride = (long long)n * w.ldm;
+        if (prepare_operand(A, n, (long long)m * n, B, m, n, true, 1.f, nullptr, at, st)) return PSVD_ERR_CUDA;
+    }
+    if (cudaGetLastError() != cudaSuccess) return PSVD_ERR_CUDA;
+    const int predicted = o.schedule == PSVD_SCHED_CANS ? predict_steps(sched, o.tol) : 12;
+    if (int rc = run_iteration(w, predicted, o.tol, learned, w.fres, st)) return rc;
+    if (learned) {
+        // matrices whose learned schedule missed tol within budget: conservative rerun
+        fallback_reset_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, prec0, w.fallback, w.done, w.prec, w.misc);
+        count_launch(1);
+        int nfb = 0;
+        if (int rc = read_int(w.misc, st, &nfb)) return rc;
+        if (nfb > 0) {
+            CoefTable ct;
+            memset(&ct, 0, sizeof(ct));
+            ct.len = (int)cons.size();
+            for (int i = 0; i < ct.len; ++i) { ct.c1[i] = (float)cons[i].c1; ct.c3[i] = (float)cons[i].c3; }
+            schedule_fill_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, w.kcap + 1, ct, nullptr, 0, o.tol, 0,
+                                                                  w.fallback, w.coef, w.budget);
+            count_launch(1);
+            if (cudaMemsetAsync(w.res, 0, sizeof(double) * (size_t)(w.kcap + 2) * B, st) ||
+                cudaMemsetAsync(w.notdone, 0, sizeof(int) * (size_t)(w.kcap + 2), st))
+                return PSVD_ERR_CUDA;
+            if (int rc = prepare_x0(A, w, st, w.done)) return rc;
+            if (int rc = run_iteration(w, predict_steps(cons, o.tol), o.tol, false, w.fres, st)) return rc;
+        }
+        set_all_done_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, w.done);
+        count_launch(1);
+    }
+    // W out + final split layouts
+    {
+        dim3 g((n + 31) / 32, (m + 31) / 32, B), blk(32, 8);
+        polar_finalize_kernel<<<g, blk, 0, st>>>(m, n, B, w.fin, w.prec, w.status, w, W);
+        count_launch(1);
+    }
+    if (want_h) {
+        MatView ahi = view_of(w.XThi[0], n, m, w.ldm, (long long)n * w.ldm, B);
+        MatView alo = view_of(w.XTlo[0], n, m, w.ldm, (long long)n * w.ldm, B);
+        MatView bhi = view_of(w.AThi, n, m, w.ldm, (long long)n * w.ldm, B);
+        MatView blo = view_of(w.ATlo, n, m, w.ldm, (long long)n * w.ldm, B);
+        GemmShape s;
+        memset(&s, 0, sizeof(s));
+        s.M = n; s.N = n; s.K = m; s.prec_uniform = PREC_TF32X3; s.err = w.err;
+        EpiStore e = epi_store_plain(w.Hraw, n, (long long)n * n, n, n);
+        if (launch_gemm(nullptr, nullptr, &ahi, &alo, &bhi, &blo, s, B, e, st) != cudaSuccess) return PSVD_ERR_CUDA;
+        dim3 g((n + 15) / 16, (n + 15) / 16, B), blk(16, 16);
+        symmetrize_kernel<<<g, blk, 0, st>>>(w.Hraw, n, w.Hsym, H_out);
+        count_launch(1);
+    }
+    if (info) {
+        polar_info_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, w.status, w.fin, w.steps, w.fallback, w.fres, w.scale,
+                                                           info);
+        count_launch(1);
+    }
+    return cudaGetLastError() == cudaSuccess ? PSVD_OK : PSVD_ERR_CUDA;
+}
+
+}  // namespace psvd
+
+// ------------------------------------------------------------ C ABI
+using namespace psvd;
+
+static bool opts_ok(const psvd_opts &o) {
+    return (o.precision == PSVD_PREC_FP32 || o.precision == PSVD_PREC_MIXED) &&
+           (o.schedule >= PSVD_SCHED_CANS && o.schedule <= PSVD_SCHED_NS) && o.delta > 0 && o.delta < 1 &&
+           o.pre_iters >= 0 && o.pre_iters <= 8 && o.max_iter >= 1 && o.max_iter <= 64 && o.tol > 0 &&
+           o.eps_qr > 0 && (o.schedule != PSVD_SCHED_LEARNED || o.lower_bound != nullptr);
+}
+
+static psvd_opts resolve_opts(const psvd_opts *p) {
+    psvd_opts o;
+    psvd_default_opts(&o);
+    if (p) o = *p;
+    return o;
+}
+
+extern "C" size_t psvd_polar_workspace_bytes(int64_t batch, int64_t m, int64_t n, const psvd_opts *opts) {
+    psvd_opts o = resolve_opts(opts);
+    if (batch <= 0 || m <= 0 || n <= 0) return 0;
+    Sizer s;
+    PolarWS w;
+    w.carve(s, (int)batch, (int)m, (int)n, polar_kcap(o), o.precision == PSVD_PREC_MIXED);
+    return s.used + 256;
+}
+
+extern "C" int psvd_polar_fwd(const float *A, float *W, float *H, int64_t batch, int64_t m, int64_t n,
+                              const psvd_opts *opts, void *ws, size_t ws_bytes, psvd_info *info, void *stream) {
+    psvd_opts o = resolve_opts(opts);
+    if (!A || !W || batch <= 0 || n <= 0 || m < n || batch > 65535 || m > (1 << 28) / 1 || !opts_ok(o))
+        return PSVD_ERR_ARG;
+    if ((long long)m * n > (1LL << 31)) return PSVD_ERR_ARG;
+    if (int e = check_device()) return e;
+    if (ws_bytes < psvd_polar_workspace_bytes(batch, m, n, &o)) return PSVD_ERR_WORKSPACE;
+    Carver cv(ws, ws_bytes);
+    PolarWS w;
+    w.carve(cv, (int)batch, (int)m, (int)n, polar_kcap(o), o.precision == PSVD_PREC_MIXED);
+    if (cv.overflow) return PSVD_ERR_WORKSPACE;
+    return polar_forward(A, W, H, H != nullptr, w, o, info, static_cast<cudaStream_t>(stream));
+}

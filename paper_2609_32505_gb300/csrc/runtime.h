@@ -1,0 +1,45 @@
+// Host-side helpers shared by the entry points.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/psvd.h"
+
+namespace psvd {
+
+int check_device();
+void count_launch(int n);
+
+inline long long round_up(long long x, long long a) { return (x + a - 1) / a * a; }
+
+// Bump allocator over a caller-provided workspace; every block is 256-byte aligned.
+struct Carver {
+    char *base;
+    size_t cap, used = 0;
+    bool overflow = false;
+    Carver(void *p, size_t c) : base(static_cast<char *>(p)), cap(c) {}
+    template <class T>
+    T *take(size_t count) {
+        size_t off = (size_t)round_up((long long)used, 256);
+        size_t bytes = count * sizeof(T);
+        used = off + bytes;
+        if (!base || used > cap) { overflow = true; return nullptr; }
+        return reinterpret_cast<T *>(base + off);
+    }
+};
+
+// Sizing pass: same carving sequence with a null base.
+struct Sizer {
+    size_t used = 0;
+    template <class T>
+    T *take(size_t count) {
+        used = (size_t)round_up((long long)used, 256) + count * sizeof(T);
+        return nullptr;
+    }
+};
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? PSVD_OK : PSVD_ERR_CUDA; }
+
+}  // namespace psvd
