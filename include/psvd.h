@@ -179,8 +179,22 @@ int psvd_gemm_tn(const float *A, const float *B, float *D, int64_t batch, int64_
 
 /* ---- misc ------------------------------------------------------------------ */
 const char *psvd_status_string(int status);
+/* Where the most recent PSVD_ERR_CUDA of this process came from (CUDA error name and
+ * source location), or "" if none; a static string owned by the library. */
+const char *psvd_last_error(void);
 /* Number of kernels this library has launched in the calling process (all threads). */
 uint64_t psvd_kernel_launch_count(void);
+
+/* Measurement hooks (no counterpart in the paper; used by the benchmark's roofline).
+ * psvd_profile_enable(1) makes every launch of the tcgen05 product kernel record a pair of
+ * CUDA events on its stream (up to 8192 launches; the call creates the events once), 0
+ * turns it off.  psvd_profile_read fills 16 doubles: for precision class c = 0 BF16,
+ * 1 TF32, 2 split-TF32, 3 per-matrix (mixed) -- out[4c] launches, out[4c+1] summed
+ * kernel milliseconds, out[4c+2] summed algorithmic flops (2MNK, M(M+1)K for the
+ * symmetric Gram), out[4c+3] longest launch in ms -- then clears the record.  Host
+ * pointer; synchronizes on the recorded events. */
+int psvd_profile_enable(int on);
+int psvd_profile_read(double *out);
 
 #ifdef __cplusplus
 }

@@ -168,4 +168,36 @@ PSVD_DEV float warp_max(float v) {
     return v;
 }
 
+constexpr uint32_t kBarrierSpin = 1u << 24;
+
+// Group barrier over `g` co-resident CTAs (cooperative launch): monotonic counter,
+// bounded spin; on expiry (or an error raised elsewhere) it records the error and
+// lets the CTA run on so that every CTA terminates.
+PSVD_DEV void group_barrier(unsigned *ctr, unsigned target, unsigned *err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+        for (uint32_t i = 0;; ++i) {
+            if (*(volatile unsigned *)ctr >= target) break;
+            if (*(volatile unsigned *)err) break;
+            if (i > kBarrierSpin) { atomicOr(err, DEV_ERR_TIMEOUT); break; }
+            __nanosleep(40);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+PSVD_DEV double block_sum(double v, double *red) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    return t;
+}
+
 }  // namespace psvd

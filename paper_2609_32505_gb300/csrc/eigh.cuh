@@ -1,0 +1,76 @@
+// Symmetric eigensolver for H = V Sigma V^T (Algorithm 1 step 5).
+#pragma once
+#include <algorithm>
+
+#include "ops.cuh"
+
+namespace psvd {
+
+constexpr int kWY = 128;   // reflectors per compact-WY block in the back-transform
+
+struct EighWS {
+    int B = 0, n = 0, nblk = 0, chunk = 0;
+    long long ldn = 0;
+    float *Aw = nullptr;          // working copy of H (n x n per matrix)
+    float *Vh = nullptr;          // Householder vectors as rows (n x ldn), v_k[k+1] = 1
+    float *tau = nullptr;         // [B][n]
+    double *d = nullptr, *e = nullptr, *lam = nullptr;   // tridiagonal and eigenvalues [B][n]
+    float *pbuf = nullptr;        // [groups][2][n]
+    unsigned *bar = nullptr;      // [groups] barrier counters
+    float *Vhi = nullptr, *Vlo = nullptr;      // Householder rows split (n x ldn)
+    float *Yhi = nullptr, *Ylo = nullptr;      // Householder vectors as columns (n x ldn)
+    float *VThi = nullptr, *VTlo = nullptr;    // current V^T split (n x ldn)
+    float *S = nullptr;                        // V^T Y for one block (n x kWY)
+    float *S2hi = nullptr, *S2lo = nullptr;    // S T^T split (n x kWY)
+    float *Tm = nullptr;                       // [B][nblk][kWY][kWY]
+    double *xs = nullptr;                      // inverse-iteration vectors, interleaved [n][chunk]
+    double *u0 = nullptr, *u1 = nullptr, *u2 = nullptr, *lm = nullptr;
+    signed char *piv = nullptr;
+    unsigned *err = nullptr;
+    int groups = 0;
+
+    template <class C>
+    void carve(C &cv, int B_, int n_, int groups_) {
+        B = B_; n = n_; groups = groups_;
+        ldn = pad_ld(n);
+        nblk = n > 2 ? (n - 2 + kWY - 1) / kWY : 0;
+        const long long B64 = B, nn = (long long)n * ldn;
+        // inverse-iteration scratch holds whole matrices: n vectors x n entries each
+        chunk = n * (int)std::max<long long>(1, std::min<long long>(B64, (1LL << 24) / ((long long)n * n)));
+        Aw = cv.template take<float>(B64 * n * n);
+        Vh = cv.template take<float>(B64 * nn);
+        tau = cv.template take<float>(B64 * n);
+        d = cv.template take<double>(B64 * n);
+        e = cv.template take<double>(B64 * n);
+        lam = cv.template take<double>(B64 * n);
+        pbuf = cv.template take<float>((long long)groups * 2 * n);
+        bar = cv.template take<unsigned>(groups + 1);
+        Vhi = cv.template take<float>(B64 * nn);
+        Vlo = cv.template take<float>(B64 * nn);
+        Yhi = cv.template take<float>(B64 * nn);
+        Ylo = cv.template take<float>(B64 * nn);
+        VThi = cv.template take<float>(B64 * nn);
+        VTlo = cv.template take<float>(B64 * nn);
+        S = cv.template take<float>(B64 * n * kWY);
+        S2hi = cv.template take<float>(B64 * n * kWY);
+        S2lo = cv.template take<float>(B64 * n * kWY);
+        Tm = cv.template take<float>(B64 * (nblk > 0 ? nblk : 1) * kWY * kWY);
+        xs = cv.template take<double>((long long)n * chunk);
+        u0 = cv.template take<double>((long long)n * chunk);
+        u1 = cv.template take<double>((long long)n * chunk);
+        u2 = cv.template take<double>((long long)n * chunk);
+        lm = cv.template take<double>((long long)n * chunk);
+        piv = cv.template take<signed char>((long long)n * chunk);
+        err = cv.template take<unsigned>(4);
+    }
+};
+
+int eigh_groups(int B, int n);
+
+// Eigendecomposition of the symmetric matrices Hs (B x n x n, FP32, full storage).
+// Writes eigenvalues descending to S (B x n, may be null) and V^T split into
+// ws.VThi / ws.VTlo (rows = eigenvectors, largest-|.| entry positive), and V^T to
+// VT (B x n x n, may be null).
+int eigh_forward(const float *Hs, float *S, float *VT, EighWS &ws, cudaStream_t st);
+
+}  // namespace psvd

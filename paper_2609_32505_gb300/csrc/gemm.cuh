@@ -246,38 +246,56 @@ struct MatView {
 bool make_tmap(CUtensorMap *out, const MatView &v);
 
 void count_launch(int n = 1);
+int cuda_fail(cudaError_t e, const char *file, int line);
+
+// Optional per-launch timing of the product kernel (CUDA events on the launching
+// stream); `flops` is the algorithmic count of the launch, `prec` its class.
+void prof_begin(cudaStream_t st);
+void prof_end(cudaStream_t st, double flops, int prec);
+bool prof_on();
+
 
 template <class Epi>
 cudaError_t launch_gemm(const MatView *a16, const MatView *b16, const MatView *ahi, const MatView *alo,
                         const MatView *bhi, const MatView *blo, GemmShape shp, int batch, const Epi &epi,
                         cudaStream_t st) {
-    static bool configured = false;
-    if (!configured) {
+    // Set on every launch, through the same kernel handle the launch below uses: each
+    // .cu file that instantiates this template registers its own copy of the kernel, so
+    // a process-wide "already configured" flag would leave other copies unconfigured.
+    {
         cudaError_t e = cudaFuncSetAttribute(gemm_tn_kernel<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              kGemmSmem);
-        if (e != cudaSuccess) return e;
-        configured = true;
+        if (e != cudaSuccess) { cuda_fail(e, __FILE__, __LINE__); return e; }
     }
     GemmMaps maps;
     memset(&maps, 0, sizeof(maps));
     // Any map that is not supplied aliases a supplied one of the same role; the
     // kernel only dereferences the maps of the precision it runs.
     const MatView *A32 = ahi ? ahi : alo, *B32 = bhi ? bhi : blo;
-    if (a16 && !make_tmap(&maps.a_bf16, *a16)) return cudaErrorInvalidValue;
-    if (b16 && !make_tmap(&maps.b_bf16, *b16)) return cudaErrorInvalidValue;
-    if (A32 && !make_tmap(&maps.a_hi, *A32)) return cudaErrorInvalidValue;
-    if (alo && !make_tmap(&maps.a_lo, *alo)) return cudaErrorInvalidValue;
-    if (B32 && !make_tmap(&maps.b_hi, *B32)) return cudaErrorInvalidValue;
-    if (blo && !make_tmap(&maps.b_lo, *blo)) return cudaErrorInvalidValue;
+    if ((a16 && !make_tmap(&maps.a_bf16, *a16)) || (b16 && !make_tmap(&maps.b_bf16, *b16)) ||
+        (A32 && !make_tmap(&maps.a_hi, *A32)) || (alo && !make_tmap(&maps.a_lo, *alo)) ||
+        (B32 && !make_tmap(&maps.b_hi, *B32)) || (blo && !make_tmap(&maps.b_lo, *blo))) {
+        cuda_fail(cudaErrorInvalidValue, "tensor map encode", __LINE__);
+        return cudaErrorInvalidValue;
+    }
     shp.tiles_m = (shp.M + kBM - 1) / kBM;
     shp.tiles_n = (shp.N + kBN - 1) / kBN;
     dim3 grid;
     if (shp.sym) grid = dim3(shp.tiles_m * (shp.tiles_m + 1) / 2, 1, batch);
     else grid = dim3(shp.tiles_n, shp.tiles_m, batch);
     if (grid.x == 0 || grid.y == 0 || batch == 0) return cudaSuccess;
+    const bool prof = prof_on();
+    if (prof) prof_begin(st);
     gemm_tn_kernel<Epi><<<grid, kGemmThreads, kGemmSmem, st>>>(maps, shp, epi);
     count_launch();
-    return cudaGetLastError();
+    if (prof) {
+        // algorithmic flops: 2 M N K per matrix (M (M + 1) K for the symmetric Gram)
+        const double f = shp.sym ? (double)shp.M * (shp.M + 1) * shp.K : 2.0 * shp.M * shp.N * (double)shp.K;
+        prof_end(st, f * batch, shp.prec ? -1 : shp.prec_uniform);
+    }
+    cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) cuda_fail(le, __FILE__, __LINE__);
+    return le;
 }
 
 }  // namespace psvd

@@ -1,0 +1,312 @@
+// Learned lower bound for the polynomial schedule: sketch features of the
+// normalized matrix and a small MLP (8 -> 64 -> 64 -> 1, ReLU) trained with Adam on
+// spectra the method itself produces.  The predicted value is log of a lower bound on
+// sigma_min(X0); the schedule then starts from [l, 1] (greedy optimal cubics) and a
+// matrix whose residual misses the tolerance within budget is rerun with the
+// conservative CANS schedule.
+#include <cmath>
+#include <cstring>
+
+#include "ops.cuh"
+
+namespace psvd {
+
+__global__ void norm_panel_kernel(const float *__restrict__ A, int m, int n, float *rowsum, float *colsum,
+                                  int *nonfinite);
+__global__ void norm_finalize_kernel(const float *rowsum, const float *colsum, const int *nonfinite, int m, int n,
+                                     float *scale, int *done, int *status, int *fin);
+
+constexpr int kH = 64, kF = 8;
+constexpr int kP_W1 = 0, kP_b1 = kH * kF, kP_W2 = kP_b1 + kH, kP_b2 = kP_W2 + kH * kH, kP_W3 = kP_b2 + kH,
+              kP_b3 = kP_W3 + kH, kNP = kP_b3 + 1;
+static_assert(kNP == PSVD_MLP_NPARAMS, "parameter layout");
+
+struct SketchWS {
+    float *rowsum, *colsum, *scale, *T, *Y, *acc, *fro;
+    int *nonfinite, *done, *status, *fin;
+    template <class C>
+    void carve(C &cv, long long B, long long m, long long n, long long s) {
+        rowsum = cv.template take<float>(B * m);
+        colsum = cv.template take<float>(B * n);
+        scale = cv.template take<float>(B);
+        T = cv.template take<float>(B * m * s);
+        Y = cv.template take<float>(B * n * s);
+        acc = cv.template take<float>(B * 4);
+        fro = cv.template take<float>(B);
+        nonfinite = cv.template take<int>(B);
+        done = cv.template take<int>(B);
+        status = cv.template take<int>(B);
+        fin = cv.template take<int>(B);
+    }
+};
+
+// out[b][i][p] = (1/scale_b) sum_k A[b][i][k] Y[b][k][p]     (X0 Y, one warp per (b, i))
+__global__ void xy_kernel(const float *A, const float *scale, const float *Y, int m, int n, int s, float *out) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.y;
+    if (warp >= m) return;
+    const float *a = A + (long long)b * m * n + (long long)warp * n;
+    const float *y = Y + (long long)b * n * s;
+    const float sc = scale[b] > 0.f ? 1.f / scale[b] : 0.f;
+    float acc[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) acc[p] = 0.f;
+    for (int k = lane; k < n; k += 32) {
+        const float x = a[k] * sc;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) if (p < s) acc[p] += x * y[(long long)k * s + p];
+    }
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+        const float v = warp_sum(acc[p]);
+        if (lane == 0 && p < s) out[(long long)b * m * s + (long long)warp * s + p] = v;
+    }
+}
+
+// out[b][k][p] = (1/scale_b) sum_i A[b][i][k] T[b][i][p]     (X0^T T, one thread per (b, k))
+__global__ void xty_kernel(const float *A, const float *scale, const float *T, int m, int n, int s, float *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (k >= n) return;
+    const float *a = A + (long long)b * m * n;
+    const float *t = T + (long long)b * m * s;
+    const float sc = scale[b] > 0.f ? 1.f / scale[b] : 0.f;
+    float acc[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) acc[p] = 0.f;
+    for (int i = 0; i < m; ++i) {
+        const float x = a[(long long)i * n + k] * sc;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) if (p < s) acc[p] += x * t[(long long)i * s + p];
+    }
+#pragma unroll
+    for (int p = 0; p < 8; ++p) if (p < s) out[(long long)b * n * s + (long long)k * s + p] = acc[p];
+}
+
+// acc[b][j] += sum z .* y  (Hutchinson term for power j)
+__global__ void zdot_kernel(const float *Z, const float *Y, int n, int s, int j, float *acc) {
+    __shared__ float red[32];
+    const int b = blockIdx.x;
+    float v = 0.f;
+    for (long long i = threadIdx.x; i < (long long)n * s; i += blockDim.x)
+        v += Z[(long long)b * n * s + i] * Y[(long long)b * n * s + i];
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        acc[b * 4 + j] = t;
+    }
+}
+
+__global__ void fro_kernel(const float *A, const float *scale, long long mn, float *fro) {
+    __shared__ double red[32];
+    const int b = blockIdx.x;
+    const float sc = scale[b] > 0.f ? 1.f / scale[b] : 0.f;
+    double v = 0.0;
+    for (long long i = threadIdx.x; i < mn; i += blockDim.x) {
+        const double x = (double)A[(long long)b * mn + i] * sc;
+        v += x * x;
+    }
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        fro[b] = (float)t;
+    }
+}
+
+__global__ void features_kernel(const float *acc, const float *fro, int B, int m, int n, int s, float *F) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const float inv = 1.f / ((float)n * (float)s);
+    const float tiny = 1e-30f;
+    float t[4];
+    for (int j = 0; j < 4; ++j) t[j] = acc[b * 4 + j] * inv;
+    float *f = F + (long long)b * kF;
+    f[0] = t[0]; f[1] = t[1]; f[2] = t[2]; f[3] = t[3];
+    f[4] = logf(fmaxf(fro[b] / (float)n, tiny));
+    f[5] = logf(fmaxf(t[3], tiny) / fmaxf(t[2], tiny));
+    f[6] = logf((float)n) / 10.f;
+    f[7] = logf((float)m / (float)n);
+}
+
+// ------------------------------------------------------------ MLP
+// One thread per sample; parameters staged in shared memory.
+__global__ void mlp_fwd_kernel(const float *params, const float *F, int nb, float *Y) {
+    __shared__ float P[kNP];
+    for (int i = threadIdx.x; i < kNP; i += blockDim.x) P[i] = params[i];
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb) return;
+    float f[kF], h1[kH];
+#pragma unroll
+    for (int i = 0; i < kF; ++i) f[i] = F[(long long)t * kF + i];
+    for (int o = 0; o < kH; ++o) {
+        float z = P[kP_b1 + o];
+#pragma unroll
+        for (int i = 0; i < kF; ++i) z += P[kP_W1 + o * kF + i] * f[i];
+        h1[o] = fmaxf(z, 0.f);
+    }
+    float y = P[kP_b3];
+    for (int o = 0; o < kH; ++o) {
+        float z = P[kP_b2 + o];
+        for (int i = 0; i < kH; ++i) z += P[kP_W2 + o * kH + i] * h1[i];
+        y += P[kP_W3 + o] * fmaxf(z, 0.f);
+    }
+    Y[t] = y;
+}
+
+// Gradients of 0.5 mean (y - target)^2; block-level accumulation in shared memory.
+__global__ void mlp_grad_kernel(const float *params, const float *F, const float *target, int nb, float *grads,
+                                float *loss) {
+    __shared__ float P[kNP];
+    __shared__ float G[kNP];
+    __shared__ float lsum;
+    for (int i = threadIdx.x; i < kNP; i += blockDim.x) { P[i] = params[i]; G[i] = 0.f; }
+    if (threadIdx.x == 0) lsum = 0.f;
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nb) {
+        float f[kF], z1[kH], h1[kH], z2[kH];
+#pragma unroll
+        for (int i = 0; i < kF; ++i) f[i] = F[(long long)t * kF + i];
+        for (int o = 0; o < kH; ++o) {
+            float z = P[kP_b1 + o];
+#pragma unroll
+            for (int i = 0; i < kF; ++i) z += P[kP_W1 + o * kF + i] * f[i];
+            z1[o] = z;
+            h1[o] = fmaxf(z, 0.f);
+        }
+        float y = P[kP_b3];
+        for (int o = 0; o < kH; ++o) {
+            float z = P[kP_b2 + o];
+            for (int i = 0; i < kH; ++i) z += P[kP_W2 + o * kH + i] * h1[i];
+            z2[o] = z;
+            y += P[kP_W3 + o] * fmaxf(z, 0.f);
+        }
+        const float r = y - target[t];
+        atomicAdd(&lsum, 0.5f * r * r / nb);
+        const float dy = r / nb;
+        atomicAdd(&G[kP_b3], dy);
+        float dh1[kH];
+        for (int i = 0; i < kH; ++i) dh1[i] = 0.f;
+        for (int o = 0; o < kH; ++o) {
+            const float h2 = fmaxf(z2[o], 0.f);
+            atomicAdd(&G[kP_W3 + o], dy * h2);
+            const float dz2 = z2[o] > 0.f ? dy * P[kP_W3 + o] : 0.f;
+            if (dz2 != 0.f) {
+                atomicAdd(&G[kP_b2 + o], dz2);
+                for (int i = 0; i < kH; ++i) {
+                    atomicAdd(&G[kP_W2 + o * kH + i], dz2 * h1[i]);
+                    dh1[i] += dz2 * P[kP_W2 + o * kH + i];
+                }
+            }
+        }
+        for (int o = 0; o < kH; ++o) {
+            const float dz1 = z1[o] > 0.f ? dh1[o] : 0.f;
+            if (dz1 != 0.f) {
+                atomicAdd(&G[kP_b1 + o], dz1);
+#pragma unroll
+                for (int i = 0; i < kF; ++i) atomicAdd(&G[kP_W1 + o * kF + i], dz1 * f[i]);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kNP; i += blockDim.x)
+        if (G[i] != 0.f) atomicAdd(&grads[i], G[i]);
+    if (threadIdx.x == 0 && loss) atomicAdd(loss, lsum);
+}
+
+__global__ void adam_kernel(float *params, const float *grads, float *m1, float *m2, float lr, float b1t, float b2t) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kNP) return;
+    const float g = grads[i];
+    const float a = 0.9f * m1[i] + 0.1f * g;
+    const float b = 0.999f * m2[i] + 0.001f * g * g;
+    m1[i] = a;
+    m2[i] = b;
+    const float mh = a / (1.f - b1t), vh = b / (1.f - b2t);
+    params[i] -= lr * mh / (sqrtf(vh) + 1e-8f);
+}
+
+}  // namespace psvd
+
+using namespace psvd;
+
+extern "C" size_t psvd_sketch_workspace_bytes(int64_t batch, int64_t m, int64_t n, int64_t s) {
+    if (batch <= 0 || m <= 0 || n <= 0 || s <= 0) return 0;
+    Sizer z;
+    SketchWS w;
+    w.carve(z, batch, m, n, s);
+    return z.used + 256;
+}
+
+extern "C" int psvd_sketch_features(const float *A, const float *Z, int64_t s, float *F, int64_t batch, int64_t m,
+                                    int64_t n, void *ws, size_t ws_bytes, void *stream) {
+    if (!A || !Z || !F || batch <= 0 || n <= 0 || m < n || s < 1 || s > 8 || batch > 65535) return PSVD_ERR_ARG;
+    if (int e = check_device()) return e;
+    if (ws_bytes < psvd_sketch_workspace_bytes(batch, m, n, s)) return PSVD_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Carver cv(ws, ws_bytes);
+    SketchWS w;
+    w.carve(cv, batch, m, n, s);
+    if (cv.overflow) return PSVD_ERR_WORKSPACE;
+    const int B = (int)batch, M = (int)m, Nn = (int)n, S = (int)s;
+    PSVD_TRY(cudaMemsetAsync(w.rowsum, 0, sizeof(float) * batch * m, st));
+    PSVD_TRY(cudaMemsetAsync(w.colsum, 0, sizeof(float) * batch * n, st));
+    PSVD_TRY(cudaMemsetAsync(w.nonfinite, 0, sizeof(int) * batch, st));
+    norm_panel_kernel<<<dim3((Nn + 31) / 32, (M + 255) / 256, B), dim3(32, 8), 0, st>>>(A, M, Nn, w.rowsum, w.colsum,
+                                                                                          w.nonfinite);
+    norm_finalize_kernel<<<B, 256, 0, st>>>(w.rowsum, w.colsum, w.nonfinite, M, Nn, w.scale, w.done, w.status, w.fin);
+    fro_kernel<<<B, 256, 0, st>>>(A, w.scale, (long long)m * n, w.fro);
+    count_launch(3);
+    // Y_{j+1} = X0^T (X0 Y_j), Y_0 = Z; f_j = <Z, Y_{j+1}> / (n s)
+    const float *Y = Z;
+    for (int j = 0; j < 4; ++j) {
+        xy_kernel<<<dim3((M * 32 + 255) / 256, B), 256, 0, st>>>(A, w.scale, Y, M, Nn, S, w.T);
+        xty_kernel<<<dim3((Nn + 127) / 128, B), 128, 0, st>>>(A, w.scale, w.T, M, Nn, S, w.Y);
+        zdot_kernel<<<B, 256, 0, st>>>(Z, w.Y, Nn, S, j, w.acc);
+        count_launch(3);
+        Y = w.Y;
+    }
+    features_kernel<<<(B + 127) / 128, 128, 0, st>>>(w.acc, w.fro, B, M, Nn, S, F);
+    count_launch(1);
+    PSVD_TRY(cudaGetLastError());
+    return PSVD_OK;
+}
+
+extern "C" int psvd_mlp_fwd(const float *params, const float *F, float *Y, int64_t nb, void *stream) {
+    if (!params || !F || !Y || nb <= 0) return PSVD_ERR_ARG;
+    if (int e = check_device()) return e;
+    mlp_fwd_kernel<<<(unsigned)((nb + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(params, F, (int)nb, Y);
+    count_launch(1);
+    PSVD_TRY(cudaGetLastError());
+    return PSVD_OK;
+}
+
+extern "C" int psvd_mlp_grad(const float *params, const float *F, const float *target, int64_t nb, float *grads,
+                             float *loss, void *stream) {
+    if (!params || !F || !target || !grads || nb <= 0) return PSVD_ERR_ARG;
+    if (int e = check_device()) return e;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PSVD_TRY(cudaMemsetAsync(grads, 0, sizeof(float) * kNP, st));
+    if (loss) PSVD_TRY(cudaMemsetAsync(loss, 0, sizeof(float), st));
+    mlp_grad_kernel<<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(params, F, target, (int)nb, grads, loss);
+    count_launch(1);
+    PSVD_TRY(cudaGetLastError());
+    return PSVD_OK;
+}
+
+extern "C" int psvd_mlp_train_step(float *params, float *grads, float *m1, float *m2, const float *F,
+                                   const float *target, int64_t nb, float lr, int step, float *loss, void *stream) {
+    if (!m1 || !m2 || step < 1) return PSVD_ERR_ARG;
+    if (int rc = psvd_mlp_grad(params, F, target, nb, grads, loss, stream)) return rc;
+    const float b1t = powf(0.9f, (float)step), b2t = powf(0.999f, (float)step);
+    adam_kernel<<<(kNP + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(params, grads, m1, m2, lr, b1t, b2t);
+    count_launch(1);
+    PSVD_TRY(cudaGetLastError());
+    return PSVD_OK;
+}

@@ -45,7 +45,9 @@ cudaError_t prepare_operand(const float *src, long long lds, long long bss, int 
     dim3 grid((cols + 31) / 32, (rows + 31) / 32, batch), block(32, 8);
     prepare_kernel<<<grid, block, 0, st>>>(src, lds, bss, rows, cols, trans ? 1 : 0, scale, scale_ptr, dst, skip);
     count_launch(1);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) cuda_fail(e, __FILE__, __LINE__);
+    return e;
 }
 
 }  // namespace psvd

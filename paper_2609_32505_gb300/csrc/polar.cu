@@ -437,7 +437,7 @@ int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &
     schedule_fill_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, w.kcap + 1, tab, o.lower_bound, learned ? 1 : 0,
                                                           o.tol, o.budget, nullptr, w.coef, w.budget);
     count_launch(1);
-    if (int rc = prepare_x0(A, w, st, w.done)) return rc;
+    if (int rc = prepare_x0(A, w, st, nullptr)) return rc;   // zero matrices get X0 = 0
     if (want_h) {
         SplitOut at;
         at.hi = w.AThi; at.lo = w.ATlo; at.ld = w.ldm; at.bstride = (long long)n * w.ldm;

@@ -2,6 +2,7 @@
 // the driver entry point (no libcuda link dependency), launch accounting, status
 // strings, workspace carving.
 #include <atomic>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 
@@ -12,8 +13,43 @@
 
 namespace psvd {
 
+static char g_err[512] = "";
 static std::atomic<uint64_t> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+// ---- product-kernel profiling (off by default) ----
+namespace {
+constexpr int kProfCap = 8192;
+struct Prof {
+    bool on = false;
+    int n = 0;
+    cudaEvent_t ev[2 * kProfCap];
+    double flops[kProfCap];
+    int prec[kProfCap];
+    bool created = false;
+} g_prof;
+std::mutex g_prof_mu;
+}  // namespace
+
+bool prof_on() { return g_prof.on; }
+
+int cuda_fail(cudaError_t e, const char *file, int line) {
+    const char *f = strrchr(file, '/');
+    snprintf(g_err, sizeof(g_err), "%s (%s) at %s:%d", cudaGetErrorName(e), cudaGetErrorString(e), f ? f + 1 : file,
+             line);
+    return PSVD_ERR_CUDA;
+}
+void prof_begin(cudaStream_t st) {
+    if (g_prof.n < kProfCap) cudaEventRecord(g_prof.ev[2 * g_prof.n], st);
+}
+void prof_end(cudaStream_t st, double flops, int prec) {
+    if (g_prof.n < kProfCap) {
+        cudaEventRecord(g_prof.ev[2 * g_prof.n + 1], st);
+        g_prof.flops[g_prof.n] = flops;
+        g_prof.prec[g_prof.n] = prec;
+        ++g_prof.n;
+    }
+}
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -37,11 +73,19 @@ bool make_tmap(CUtensorMap *out, const MatView &v) {
     cuuint64_t strides[2] = {(cuuint64_t)v.ld * esz, (cuuint64_t)v.bstride * esz};
     cuuint32_t box[3] = {(cuuint32_t)(128 / esz), 128u, 1u};
     cuuint32_t estr[3] = {1, 1, 1};
-    if ((strides[0] % 16) || (strides[1] % 16) || (reinterpret_cast<uintptr_t>(v.ptr) % 16)) return false;
+    if ((strides[0] % 16) || (strides[1] % 16) || (reinterpret_cast<uintptr_t>(v.ptr) % 16)) {
+        snprintf(g_err, sizeof(g_err), "tensor map alignment: strides=(%llu,%llu) ptr=%p",
+                 (unsigned long long)strides[0], (unsigned long long)strides[1], v.ptr);
+        return false;
+    }
     CUresult r = fn(out, v.bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
                     const_cast<void *>(v.ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        snprintf(g_err, sizeof(g_err), "cuTensorMapEncodeTiled=%d dims=(%llu,%llu,%llu) strides=(%llu,%llu) ptr=%p",
+                 (int)r, (unsigned long long)dims[0], (unsigned long long)dims[1], (unsigned long long)dims[2],
+                 (unsigned long long)strides[0], (unsigned long long)strides[1], v.ptr);
     return r == CUDA_SUCCESS;
 }
 
@@ -63,6 +107,41 @@ int check_device() {
 extern "C" {
 
 uint64_t psvd_kernel_launch_count(void) { return psvd::g_launches.load(); }
+
+const char *psvd_last_error(void) { return psvd::g_err; }
+
+int psvd_profile_enable(int on) {
+    using namespace psvd;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (on && !g_prof.created) {
+        for (int i = 0; i < 2 * kProfCap; ++i)
+            if (cudaEventCreate(&g_prof.ev[i]) != cudaSuccess) return PSVD_ERR_CUDA;
+        g_prof.created = true;
+    }
+    g_prof.on = on != 0;
+    g_prof.n = 0;
+    return PSVD_OK;
+}
+
+// out[4 * c + {0,1,2,3}] for class c = 0 (BF16), 1 (TF32), 2 (split TF32), 3 (per-matrix
+// precision): launches, total ms, total algorithmic flops, max single-launch ms.
+int psvd_profile_read(double *out) {
+    using namespace psvd;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (int i = 0; i < 16; ++i) out[i] = 0.0;
+    for (int i = 0; i < g_prof.n; ++i) {
+        if (cudaEventSynchronize(g_prof.ev[2 * i + 1]) != cudaSuccess) return PSVD_ERR_CUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]) != cudaSuccess) return PSVD_ERR_CUDA;
+        const int c = g_prof.prec[i] < 0 ? 3 : g_prof.prec[i];
+        out[4 * c] += 1.0;
+        out[4 * c + 1] += ms;
+        out[4 * c + 2] += g_prof.flops[i];
+        if (ms > out[4 * c + 3]) out[4 * c + 3] = ms;
+    }
+    g_prof.n = 0;
+    return PSVD_OK;
+}
 
 const char *psvd_status_string(int s) {
     switch (s) {

@@ -42,4 +42,18 @@ struct Sizer {
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? PSVD_OK : PSVD_ERR_CUDA; }
 
+// Records where a CUDA call failed (readable through psvd_last_error) and returns
+// PSVD_ERR_CUDA.
+int cuda_fail(cudaError_t e, const char *file, int line);
+#define PSVD_TRY(expr)                                                        \
+    do {                                                                      \
+        cudaError_t _psvd_e = (expr);                                         \
+        if (_psvd_e != cudaSuccess) return psvd::cuda_fail(_psvd_e, __FILE__, __LINE__); \
+    } while (0)
+#define PSVD_TRY_RC(expr)                                                     \
+    do {                                                                      \
+        int _psvd_rc = (expr);                                                \
+        if (_psvd_rc) return _psvd_rc;                                        \
+    } while (0)
+
 }  // namespace psvd
