@@ -66,7 +66,7 @@ typedef struct psvd_opts {
     double eps_qr;        /* QR fallback threshold on | ||U_i|| - 1 |           default 1e-5 */
     const float *lower_bound; /* DEVICE [batch]: schedule 1's lower bounds (NULL otherwise) */
     int    budget;        /* schedule 1: steps allowed before the conservative rerun
-                             (0 = automatic: predicted steps + 3)                           */
+                             (0 = automatic: predicted steps + 5)                           */
 } psvd_opts;
 
 /* Fills *o with the defaults above (host pointer). */

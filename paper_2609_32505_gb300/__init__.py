@@ -347,6 +347,17 @@ def mlp_train(params: torch.Tensor, feats: torch.Tensor, target: torch.Tensor, s
     return curve
 
 
+def mlp_calibrate(params: torch.Tensor, feats: torch.Tensor, target: torch.Tensor, quantile: float = 0.98) -> float:
+    """Safety margin for the predicted lower bound: exp(-q) with q the given quantile of the
+    over-prediction y - target on (held-out) training data, so that about that fraction of
+    bounds are true lower bounds; over-predictions are caught by the conservative rerun."""
+    y = mlp_forward(params, feats)
+    over = (y - target.float()).detach().cpu().numpy()
+    import numpy as _np
+    q = float(_np.quantile(over, quantile))
+    return float(_np.exp(-max(q, 0.0)))
+
+
 def predict_lower_bound(a: torch.Tensor, params: torch.Tensor, margin: float = 0.5, probes: int = 8,
                         seed: int = 0) -> torch.Tensor:
     """Per-matrix lower bound of sigma_min(X0) for the learned schedule: margin * exp(MLP(features))."""

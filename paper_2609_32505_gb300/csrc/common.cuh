@@ -189,6 +189,41 @@ PSVD_DEV void group_barrier(unsigned *ctr, unsigned target, unsigned *err) {
     __syncthreads();
 }
 
+// Flag barrier over `g` co-resident CTAs: CTA c publishes arrive[c] = gen; CTA 0 polls all
+// arrival flags in parallel and publishes release = gen, which every other CTA polls.
+// Every wait is bounded and stops at once when the error word is raised elsewhere.
+PSVD_DEV void flag_barrier(unsigned *arrive, unsigned *release, int cig, int g, unsigned gen, unsigned *err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        *(volatile unsigned *)&arrive[cig] = gen;
+    }
+    if (cig == 0) {
+        for (int c = threadIdx.x; c < g; c += blockDim.x) {
+            for (uint32_t i = 0;; ++i) {
+                if (*(volatile unsigned *)&arrive[c] >= gen) break;
+                if (*(volatile unsigned *)err) break;
+                if (i > kBarrierSpin) { atomicOr(err, DEV_ERR_TIMEOUT); break; }
+                __nanosleep(20);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            *(volatile unsigned *)release = gen;
+        }
+    } else if (threadIdx.x == 0) {
+        for (uint32_t i = 0;; ++i) {
+            if (*(volatile unsigned *)release >= gen) break;
+            if (*(volatile unsigned *)err) break;
+            if (i > kBarrierSpin) { atomicOr(err, DEV_ERR_TIMEOUT); break; }
+            __nanosleep(20);
+        }
+    }
+    __threadfence();
+    __syncthreads();
+}
+
 PSVD_DEV double block_sum(double v, double *red) {
     v = warp_sum(v);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;

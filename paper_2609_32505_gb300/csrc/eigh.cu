@@ -25,111 +25,260 @@ struct TrdParams {
     double *d, *e;
     float *pbuf;
     unsigned *bar, *err;
-    int B, n, groups, g;
+    int B, n, groups, g, nrp;
     long long ldn;
 };
 
-__global__ void __launch_bounds__(kTrdThreads) sytrd_kernel(TrdParams P) {
-    extern __shared__ float sm[];
+// Householder step data: x (row k, columns > k, corrected) -> v (v[k+1] = 1), tau, beta.
+// Every CTA computes it redundantly from the same inputs, so no broadcast is needed.
+PSVD_DEV void householder_from_row(float *bx, int k, int n, double *red, float &ftau, double &beta_out) {
+    double s2 = 0.0;
+    for (int j = k + 2 + threadIdx.x; j < n; j += blockDim.x) s2 += (double)bx[j] * bx[j];
+    s2 = block_sum(s2, red);
+    const double alpha = bx[k + 1];
+    double beta, tau, scal;
+    if (s2 == 0.0) { beta = alpha; tau = 0.0; scal = 0.0; }
+    else {
+        beta = -copysign(sqrt(alpha * alpha + s2), alpha);
+        tau = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+    }
+    __syncthreads();
+    for (int j = k + 2 + threadIdx.x; j < n; j += blockDim.x) bx[j] = (float)(bx[j] * scal);
+    if (threadIdx.x == 0) bx[k + 1] = 1.f;
+    __syncthreads();
+    ftau = (float)tau;
+    beta_out = beta;
+}
+
+// dst[j] = src[j] for j in [jstart, n) (16-byte aligned float4 loads, all issued before
+// the stores); entries of the first partial vector below jstart are copied too.
+PSVD_DEV void load_vec4(float *dst, const float *src, int jstart, int n) {
+    const int c0 = jstart >> 2, c1 = (n + 3) >> 2;
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    float4 r[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int c = c0 + threadIdx.x + u * blockDim.x;
+        if (c < c1) r[u] = s4[c];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int c = c0 + threadIdx.x + u * blockDim.x;
+        if (c < c1) d4[c] = r[u];
+    }
+    for (int c = c0 + threadIdx.x + 4 * blockDim.x; c < c1; c += blockDim.x) d4[c] = s4[c];
+}
+
+// dst[j] = row[j] - (vk w[j] + wk v[j]) for j >= jstart, 0 below (row k+1 corrected by
+// the pending rank-2 update of step k).
+PSVD_DEV void corrected_row_vec4(float *dst, const float *row, const float *v, const float *w, float vk, float wk,
+                                 int jstart, int n) {
+    const int c1 = (n + 3) >> 2;
+    const float4 *r4 = reinterpret_cast<const float4 *>(row);
+    for (int c = threadIdx.x; c < c1; c += 4 * blockDim.x) {
+        float4 r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (c + u * (int)blockDim.x < c1 && 4 * (c + u * (int)blockDim.x) + 3 >= jstart) r[u] = r4[c + u * blockDim.x];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int cc = c + u * blockDim.x;
+            if (cc >= c1) break;
+            const float x[4] = {r[u].x, r[u].y, r[u].z, r[u].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = 4 * cc + e;
+                dst[j] = (j >= jstart && j < n) ? x[e] - (vk * w[j] + wk * v[j]) : 0.f;
+            }
+        }
+    }
+}
+
+// One pass over an owned row i: optional rank-2 update with (u_v, u_w) on columns
+// >= jstart, and optional dot product of the updated row with s_v (same columns).
+// Rows are padded to 16-byte multiples; columns < jstart are rewritten unchanged.
+template <bool kUpd, bool kDot>
+PSVD_DEV float row_pass(float *Ai, int jstart, int n, const float *uv, const float *uw, float uvi, float uwi,
+                        const float *sv) {
+    constexpr int U = 4;      // float4 loads in flight per lane
+    const int lane = threadIdx.x & 31;
+    const int cs = jstart >> 2, c1 = (n + 3) >> 2;
+    float4 *A4 = reinterpret_cast<float4 *>(Ai);
+    const float4 *V4 = reinterpret_cast<const float4 *>(uv);
+    const float4 *W4 = reinterpret_cast<const float4 *>(uw);
+    const float4 *S4 = reinterpret_cast<const float4 *>(sv);
+    float acc = 0.f;
+    // the chunk holding jstart: columns below jstart are left as they are
+    if (lane == 0 && cs < c1) {
+        float4 a = A4[cs];
+        float x[4] = {a.x, a.y, a.z, a.w};
+        const float4 vv = kUpd ? V4[cs] : make_float4(0, 0, 0, 0), ww = kUpd ? W4[cs] : make_float4(0, 0, 0, 0);
+        const float4 ss = kDot ? S4[cs] : make_float4(0, 0, 0, 0);
+        const float vq[4] = {vv.x, vv.y, vv.z, vv.w}, wq[4] = {ww.x, ww.y, ww.z, ww.w};
+        const float sq[4] = {ss.x, ss.y, ss.z, ss.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (4 * cs + e < jstart) continue;
+            if (kUpd) x[e] -= uvi * wq[e] + uwi * vq[e];
+            if (kDot) acc += x[e] * sq[e];
+        }
+        if (kUpd) A4[cs] = make_float4(x[0], x[1], x[2], x[3]);
+    }
+    // full chunks: entries past n are zero in the row and in every vector
+    for (int c = cs + 1 + lane; c < c1; c += 32 * U) {
+        float4 a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (c + 32 * u < c1) a[u] = A4[c + 32 * u];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int cc = c + 32 * u;
+            if (cc < c1) {
+                float4 x = a[u];
+                if (kUpd) {
+                    const float4 vv = V4[cc], ww = W4[cc];
+                    x.x -= uvi * ww.x + uwi * vv.x;
+                    x.y -= uvi * ww.y + uwi * vv.y;
+                    x.z -= uvi * ww.z + uwi * vv.z;
+                    x.w -= uvi * ww.w + uwi * vv.w;
+                    A4[cc] = x;
+                }
+                if (kDot) {
+                    const float4 ss = S4[cc];
+                    acc += x.x * ss.x + x.y * ss.y + x.z * ss.z + x.w * ss.w;
+                }
+            }
+        }
+    }
+    return kDot ? warp_sum(acc) : 0.f;
+}
+
+// Tridiagonalization Q^T H Q = T.  Step k builds the reflector from row k (columns
+// > k) of the current matrix; row k is never updated in place (the row a reflector is
+// built from is corrected on the fly with the previous step's v, w).  After the group
+// barrier of step k every CTA holds v_k and w_k, builds v_{k+1} from row k+1, and then
+// makes one pass over its owned rows that applies the rank-2 update of step k and
+// accumulates the matrix-vector product of step k+1.
+__global__ void __launch_bounds__(kTrdThreads, 2) sytrd_kernel(TrdParams P) {
+    extern __shared__ __align__(16) float sm[];
     __shared__ double red[32];
     const int n = P.n;
-    float *bx = sm, *bv = sm + n, *bw = sm + 2 * n;
+    const int ln = (int)P.ldn;
+    float *bufs[3] = {sm, sm + ln, sm + 2 * ln};
     const int grp = blockIdx.x / P.g, cig = blockIdx.x % P.g;
     if (grp >= P.groups) return;
     const int nwarp = kTrdThreads / 32, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = cig * nwarp + warp, GW = P.g * nwarp;
-    unsigned *ctr = P.bar + grp;
+    unsigned *rel = P.bar + (long long)grp * (P.g + 1);
+    unsigned *arr = rel + 1;
     unsigned nbar = 0;
+#define TRD_BARRIER() flag_barrier(arr, rel, cig, P.g, ++nbar, P.err)
     for (int b = grp; b < P.B; b += P.groups) {
         const float *Hb = P.H + (long long)b * n * n;
-        float *A = P.Aw + (long long)b * n * n;
-        float *Vh = P.Vh + (long long)b * n * P.ldn;
+        float *A = P.Aw + (long long)b * n * ln;
+        float *Vh = P.Vh + (long long)b * P.nrp * P.ldn;
+        double *D = P.d + (long long)b * n, *E = P.e + (long long)b * n;
         for (int i = gw; i < n; i += GW)
-            for (int j = lane; j < n; j += 32) A[(long long)i * n + j] = Hb[(long long)i * n + j];
-        for (int j = threadIdx.x; j < n; j += blockDim.x) { bv[j] = 0.f; bw[j] = 0.f; }
-        group_barrier(ctr, (++nbar) * P.g, P.err);
-        for (int k = 0; k + 2 < n; ++k) {
-            // x = row k (columns k+1..n-1), corrected by the deferred update of step k-1
-            const float vk = bv[k], wk = bw[k];
-            const float *Ak = A + (long long)k * n;
-            for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) bx[j] = Ak[j] - (vk * bw[j] + wk * bv[j]);
+            for (int j = lane; j < ln; j += 32) A[(long long)i * ln + j] = j < n ? Hb[(long long)i * n + j] : 0.f;
+        for (int j = threadIdx.x; j < 3 * ln; j += blockDim.x) sm[j] = 0.f;
+        TRD_BARRIER();
+        float *bv = bufs[0], *bw = bufs[1], *bn = bufs[2];   // v_k, w_k, next v
+        float tau_k = 0.f;
+        if (n >= 3) {
+            // reflector 0 from row 0, then the plain matrix-vector product of step 0
+            for (int j = 1 + threadIdx.x; j < n; j += blockDim.x) bv[j] = A[j];
             __syncthreads();
-            double s2 = 0.0;
-            for (int j = k + 2 + threadIdx.x; j < n; j += blockDim.x) s2 += (double)bx[j] * bx[j];
-            s2 = block_sum(s2, red);
-            const double alpha = bx[k + 1];
-            double beta, tau, scal;
-            if (s2 == 0.0) { beta = alpha; tau = 0.0; scal = 0.0; }
-            else {
-                beta = -copysign(sqrt(alpha * alpha + s2), alpha);
-                tau = (beta - alpha) / beta;
-                scal = 1.0 / (alpha - beta);
-            }
-            __syncthreads();
-            for (int j = k + 2 + threadIdx.x; j < n; j += blockDim.x) bx[j] = (float)(bx[j] * scal);
-            if (threadIdx.x == 0) bx[k + 1] = 1.f;
-            __syncthreads();
-            const float ftau = (float)tau;
+            double beta;
+            householder_from_row(bv, 0, n, red, tau_k, beta);
             if (cig == 0) {
-                if (threadIdx.x == 0) {
-                    P.d[(long long)b * n + k] = (double)Ak[k] - 2.0 * (double)vk * (double)wk;
-                    P.e[(long long)b * n + k] = beta;
-                    P.tau[(long long)b * n + k] = ftau;
-                }
-                for (int j = threadIdx.x; j < n; j += blockDim.x)
-                    Vh[(long long)k * P.ldn + j] = j > k ? bx[j] : 0.f;
+                if (threadIdx.x == 0) { D[0] = A[0]; E[0] = beta; P.tau[(long long)b * n] = tau_k; }
+                for (int j = threadIdx.x; j < n; j += blockDim.x) Vh[j] = j > 0 ? bv[j] : 0.f;
             }
-            // p_i = tau * (A v)_i for owned trailing rows
-            float *pb = P.pbuf + ((long long)grp * 2 + (k & 1)) * n;
+            float *pb = P.pbuf + ((long long)grp * 2 + 0) * ln;
             for (int i = gw; i < n; i += GW) {
-                if (i <= k) continue;
-                const float *Ai = A + (long long)i * n;
-                float acc = 0.f;
-                for (int j = k + 1 + lane; j < n; j += 32) acc += Ai[j] * bx[j];
-                acc = warp_sum(acc);
-                if (lane == 0) pb[i] = ftau * acc;
+                if (i < 1) continue;
+                const float acc = row_pass<false, true>(A + (long long)i * ln, 1, n, nullptr, nullptr, 0.f, 0.f, bv);
+                if (lane == 0) pb[i] = tau_k * acc;
             }
-            group_barrier(ctr, (++nbar) * P.g, P.err);
-            for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) bw[j] = pb[j];
+            TRD_BARRIER();
+        }
+        for (int k = 0; k + 2 < n; ++k) {
+            // w_k = p_k - (tau_k/2)(p_k . v_k) v_k
+            const float *pb = P.pbuf + ((long long)grp * 2 + (k & 1)) * ln;
+            load_vec4(bw, pb, k + 1, n);
             __syncthreads();
             double pv = 0.0;
-            for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) pv += (double)bw[j] * bx[j];
+            for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) pv += (double)bw[j] * bv[j];
             pv = block_sum(pv, red);
-            const float K = (float)(0.5 * tau * pv);
-            for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) bw[j] -= K * bx[j];
+            const float K = (float)(0.5 * (double)tau_k * pv);
+            for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) bw[j] -= K * bv[j];
             __syncthreads();
-            // rank-2 update of owned rows i >= k+2 (row k+1 is corrected by the next step)
+            const bool more = k + 3 < n;          // a reflector k+1 exists
+            float tau_n = 0.f;
+            if (more) {
+                // row k+1 corrected by (v_k, w_k) -> reflector k+1
+                const float vk = bv[k + 1], wk = bw[k + 1];
+                const float *Ar = A + (long long)(k + 1) * ln;
+                corrected_row_vec4(bn, Ar, bv, bw, vk, wk, k + 2, n);
+                __syncthreads();
+                double beta;
+                householder_from_row(bn, k + 1, n, red, tau_n, beta);
+                if (cig == 0) {
+                    if (threadIdx.x == 0) {
+                        D[k + 1] = (double)Ar[k + 1] - 2.0 * (double)vk * (double)wk;
+                        E[k + 1] = beta;
+                        P.tau[(long long)b * n + k + 1] = tau_n;
+                    }
+                    for (int j = threadIdx.x; j < n; j += blockDim.x)
+                        Vh[(long long)(k + 1) * P.ldn + j] = j > k + 1 ? bn[j] : 0.f;
+                }
+            }
+            // fused pass: rank-2 update of step k and matrix-vector product of step k+1
+            float *pn = P.pbuf + ((long long)grp * 2 + ((k + 1) & 1)) * ln;
             for (int i = gw; i < n; i += GW) {
                 if (i < k + 2) continue;
-                float *Ai = A + (long long)i * n;
-                const float vi = bx[i], wi = bw[i];
-                for (int j = k + 2 + lane; j < n; j += 32) Ai[j] -= vi * bw[j] + wi * bx[j];
-            }
-            float *t = bv; bv = bx; bx = t;     // v_k becomes the correction vector of step k+1
-            __syncthreads();
-        }
-        group_barrier(ctr, (++nbar) * P.g, P.err);
-        if (cig == 0) {
-            if (threadIdx.x == 0) {
-                double *d = P.d + (long long)b * n, *e = P.e + (long long)b * n;
-                if (n == 1) {
-                    d[0] = A[0];
+                float *Ai = A + (long long)i * ln;
+                if (more) {
+                    const float acc = row_pass<true, true>(Ai, k + 2, n, bv, bw, bv[i], bw[i], bn);
+                    if (lane == 0) pn[i] = tau_n * acc;
                 } else {
-                    const int k = n - 2;
-                    d[k] = (double)A[(long long)k * n + k] - 2.0 * (double)bv[k] * (double)bw[k];
-                    e[k] = (double)A[(long long)k * n + k + 1] - ((double)bv[k] * bw[k + 1] + (double)bw[k] * bv[k + 1]);
-                    d[k + 1] = A[(long long)(k + 1) * n + k + 1];
-                    P.tau[(long long)b * n + k] = 0.f;
+                    row_pass<true, false>(Ai, k + 2, n, bv, bw, bv[i], bw[i], nullptr);
                 }
-                P.tau[(long long)b * n + n - 1] = 0.f;
-                e[n - 1] = 0.0;
             }
+            if (more) {
+                TRD_BARRIER();
+                float *t = bv; bv = bn; bn = t;     // v_{k+1} becomes current
+                tau_k = tau_n;
+                __syncthreads();
+            }
+        }
+        TRD_BARRIER();
+        if (cig == 0 && threadIdx.x == 0) {
+            if (n == 1) {
+                D[0] = A[0];
+            } else {
+                // last 2 x 2 block: row n-2 still carries the pending update of the last step
+                const int k = n - 2;
+                const float vk = n >= 3 ? bv[k] : 0.f, wk = n >= 3 ? bw[k] : 0.f;
+                const float vl = n >= 3 ? bv[k + 1] : 0.f, wl = n >= 3 ? bw[k + 1] : 0.f;
+                D[k] = (double)A[(long long)k * ln + k] - 2.0 * (double)vk * (double)wk;
+                E[k] = (double)A[(long long)k * ln + k + 1] - ((double)vk * wl + (double)wk * vl);
+                D[k + 1] = A[(long long)(k + 1) * ln + k + 1];
+                P.tau[(long long)b * n + k] = 0.f;
+            }
+            P.tau[(long long)b * n + n - 1] = 0.f;
+            E[n - 1] = 0.0;
+        }
+        if (cig == 0)
             for (int r = n - 2 < 0 ? 0 : n - 2; r < n; ++r)
                 for (int j = threadIdx.x; j < n; j += blockDim.x) Vh[(long long)r * P.ldn + j] = 0.f;
-        }
-        group_barrier(ctr, (++nbar) * P.g, P.err);
+        TRD_BARRIER();
     }
 }
+
+#undef TRD_BARRIER
 
 // ------------------------------------------------------------ bisection (FP32)
 // ascending index j: the largest x with at most j eigenvalues below it.
@@ -139,7 +288,7 @@ PSVD_DEV int sturm_count(const float *d, const float *e2, int n, float x, float 
     if (fabsf(q) < pivmin) q = -pivmin;
     c += q < 0.f;
     for (int t = 1; t < n; ++t) {
-        q = d[t] - x - e2[t - 1] / q;
+        q = d[t] - x - __fdividef(e2[t - 1], q);
         if (fabsf(q) < pivmin) q = -pivmin;
         c += q < 0.f;
     }
@@ -225,41 +374,81 @@ PSVD_DEV void tri_factor(const InvitParams &P, const double *D, const double *E,
         const double dn = D[j + 1] - mu;
         const double en = j + 1 < n - 1 ? E[j + 1] : 0.0;
         if (fabs(a) >= fabs(c)) {
-            if (a == 0.0) a = tiny;
-            const double m = c / a;
-            P.u0[j * s + t] = a; P.u1[j * s + t] = bsup; P.u2[j * s + t] = 0.0; P.lm[j * s + t] = m;
+            if (fabs(a) < tiny) a = a < 0 ? -tiny : tiny;
+            const double ra = 1.0 / a;
+            const double m = c * ra;
+            P.u0[j * s + t] = ra; P.u1[j * s + t] = bsup; P.u2[j * s + t] = 0.0; P.lm[j * s + t] = m;
             P.piv[j * s + t] = 0;
             a = dn - m * bsup;
             bsup = en;
         } else {
-            const double m = a / c;
-            P.u0[j * s + t] = c; P.u1[j * s + t] = dn; P.u2[j * s + t] = en; P.lm[j * s + t] = m;
+            const double rc = 1.0 / c;
+            const double m = a * rc;
+            P.u0[j * s + t] = rc; P.u1[j * s + t] = dn; P.u2[j * s + t] = en; P.lm[j * s + t] = m;
             P.piv[j * s + t] = 1;
             a = bsup - m * dn;
             bsup = -m * en;
         }
     }
     if (fabs(a) < tiny) a = a < 0 ? -tiny : tiny;
-    P.u0[(long long)(n - 1) * s + t] = a;
+    P.u0[(long long)(n - 1) * s + t] = 1.0 / a;     // u0 holds reciprocal pivots
 }
 
+// Solves (T - mu I) x = b in place with the stored factorization and normalizes x.
+// The loops carry one or two scalars; every load is issued kPf iterations ahead.
 PSVD_DEV void tri_solve_normalize(const InvitParams &P, int n, int t) {
+    constexpr int kPf = 8;
     const long long s = P.stride;
-    double *x = P.xs;
-    for (int j = 0; j < n - 1; ++j) {
-        double xj = x[j * s + t], xn = x[(j + 1) * s + t];
-        if (P.piv[j * s + t]) { const double tmp = xj; xj = xn; xn = tmp; x[j * s + t] = xj; }
-        x[(j + 1) * s + t] = xn - P.lm[j * s + t] * xj;
+    double *__restrict__ x = P.xs;
+    const double *__restrict__ lm = P.lm;
+    const double *__restrict__ u0 = P.u0;
+    const double *__restrict__ u1 = P.u1;
+    const double *__restrict__ u2 = P.u2;
+    const signed char *__restrict__ pv = P.piv;
+    // forward: apply the row swaps and multipliers
+    double carry = x[t];
+    for (int j0 = 0; j0 < n - 1; j0 += kPf) {
+        double bx[kPf], bl[kPf];
+        signed char bp[kPf];
+#pragma unroll
+        for (int u = 0; u < kPf; ++u) {
+            const int j = j0 + u;
+            if (j < n - 1) { bx[u] = x[(j + 1) * s + t]; bl[u] = lm[j * s + t]; bp[u] = pv[j * s + t]; }
+        }
+#pragma unroll
+        for (int u = 0; u < kPf; ++u) {
+            const int j = j0 + u;
+            if (j < n - 1) {
+                double a = carry, b = bx[u];
+                if (bp[u]) { const double tmp = a; a = b; b = tmp; }
+                x[j * s + t] = a;
+                carry = b - bl[u] * a;
+            }
+        }
     }
-    double x1 = x[(long long)(n - 1) * s + t] / P.u0[(long long)(n - 1) * s + t];
+    x[(long long)(n - 1) * s + t] = carry;
+    // backward: U x = y with reciprocal pivots in u0
+    double x1 = carry * u0[(long long)(n - 1) * s + t], x2 = 0.0;
     x[(long long)(n - 1) * s + t] = x1;
-    double x2 = 0.0;
     double nrm = x1 * x1;
-    for (int j = n - 2; j >= 0; --j) {
-        const double v = (x[j * s + t] - P.u1[j * s + t] * x1 - P.u2[j * s + t] * x2) / P.u0[j * s + t];
-        x[j * s + t] = v;
-        x2 = x1; x1 = v;
-        nrm += v * v;
+    for (int j0 = n - 2; j0 >= 0; j0 -= kPf) {
+        double by[kPf], b0[kPf], b1[kPf], b2[kPf];
+#pragma unroll
+        for (int u = 0; u < kPf; ++u) {
+            const int j = j0 - u;
+            if (j >= 0) { by[u] = x[j * s + t]; b0[u] = u0[j * s + t]; b1[u] = u1[j * s + t]; b2[u] = u2[j * s + t]; }
+        }
+#pragma unroll
+        for (int u = 0; u < kPf; ++u) {
+            const int j = j0 - u;
+            if (j >= 0) {
+                const double v = (by[u] - b1[u] * x1 - b2[u] * x2) * b0[u];
+                x[j * s + t] = v;
+                x2 = x1;
+                x1 = v;
+                nrm += v * v;
+            }
+        }
     }
     const double inv = nrm > 0 ? 1.0 / sqrt(nrm) : 0.0;
     for (int j = 0; j < n; ++j) x[j * s + t] *= inv;
@@ -296,13 +485,11 @@ __global__ void tri_invit_kernel(InvitParams P) {
     }
     const double tiny = fmax(tn * 2.2e-16, 1e-280);
     for (int j = 0; j < n; ++j) P.xs[j * s + t] = hash_unit((unsigned)i, (unsigned)j) + 0.0625;
+    // the bisection shift is accurate to ~1e-7 ||T||: three solves reduce the other
+    // components by (shift error / gap)^3
     tri_factor(P, D, E, n, mu, tiny, t);
     tri_solve_normalize(P, n, t);
     tri_solve_normalize(P, n, t);
-    // refine the shift with the Rayleigh quotient and iterate once more
-    const double rq = tri_rayleigh(P, D, E, n, t);
-    if (fabs(rq - mu) < 1e-4 * fmax(tn, 1e-300)) mu = rq;
-    tri_factor(P, D, E, n, mu, tiny, t);
     tri_solve_normalize(P, n, t);
     P.lam[gi] = tri_rayleigh(P, D, E, n, t);
 }
@@ -387,26 +574,17 @@ __global__ void zt_store_kernel(const double *xs, long long stride, int n, int f
 }
 
 // ------------------------------------------------------------ back-transform
-// Upper-triangular T of the forward compact-WY form H_k0 ... H_k1-1 = I - Y T Y^T,
-// one block per (WY block, matrix): G = Y^T Y, then T[:c, c] = -tau_c T[:c, :c] G[:c, c].
-__global__ void larft_kernel(const float *Vh, const float *tau, int n, long long ldn, int nblk, float *Tm) {
+// Upper-triangular T of the forward compact-WY form H_k0 ... H_k1-1 = I - Y T Y^T, one
+// block per (WY block, matrix), from G = Y^T Y (computed on the tensor cores):
+// T[c][c] = tau_c,  T[:c, c] = -tau_c T[:c, :c] G[:c, c].
+__global__ void larft_kernel(const float *Gm, const float *tau, int n, int nblk, float *Tm) {
     extern __shared__ float sm2[];
     float *G = sm2, *T = sm2 + kWY * kWY;
     const int blk = blockIdx.x, b = blockIdx.y;
     const int k0 = blk * kWY;
     const int nb = min(kWY, n - 2 - k0);
-    const float *V = Vh + (long long)b * n * ldn;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int p = warp; p < nb * nb; p += nw) {
-        const int a = p / nb, c = p % nb;
-        if (a > c) continue;
-        const float *va = V + (long long)(k0 + a) * ldn, *vc = V + (long long)(k0 + c) * ldn;
-        float acc = 0.f;
-        for (int r = k0 + c + 1 + lane; r < n; r += 32) acc += va[r] * vc[r];
-        acc = warp_sum(acc);
-        if (lane == 0) G[a * kWY + c] = acc;
-    }
-    for (int p = threadIdx.x; p < kWY * kWY; p += blockDim.x) T[p] = 0.f;
+    const float *Gb = Gm + ((long long)b * nblk + blk) * kWY * kWY;
+    for (int p = threadIdx.x; p < kWY * kWY; p += blockDim.x) { G[p] = Gb[p]; T[p] = 0.f; }
     __syncthreads();
     const float *tb = tau + (long long)b * n + k0;
     if (threadIdx.x == 0) T[0] = tb[0];
@@ -524,26 +702,28 @@ static int num_sms() {
     return sms;
 }
 
-static int trd_ctas_per_group(int n) { return std::max(1, std::min(num_sms(), n / 32)); }
+// CTAs per matrix for the tridiagonalization (up to two per SM) and matrices in flight.
+static int trd_ctas_per_group(int n) { return std::max(1, std::min(std::min(2 * num_sms(), 320), n / 16)); }
 
 int eigh_groups(int B, int n) {
     const int g = trd_ctas_per_group(n);
-    return std::max(1, std::min(B, num_sms() / g));
+    return std::max(1, std::min(B, (2 * num_sms()) / g));
 }
 
 int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t st) {
     const int B = w.B, n = w.n;
     const long long ldn = w.ldn;
-    PSVD_TRY(cudaMemsetAsync(w.bar, 0, sizeof(unsigned) * (w.groups + 1), st));
+    PSVD_TRY(cudaMemsetAsync(w.bar, 0, sizeof(unsigned) * (size_t)w.groups * (trd_ctas_per_group(n) + 1), st));
     PSVD_TRY(cudaMemsetAsync(w.err, 0, sizeof(unsigned) * 4, st));
     PSVD_TRY(cudaMemsetAsync(w.e, 0, sizeof(double) * (size_t)B * n, st));
+    PSVD_TRY(cudaMemsetAsync(w.Vh, 0, sizeof(float) * (size_t)B * w.nrp * ldn, st));
     // 1. tridiagonalization
     {
         TrdParams P;
         P.H = Hs; P.Aw = w.Aw; P.Vh = w.Vh; P.tau = w.tau; P.d = w.d; P.e = w.e; P.pbuf = w.pbuf;
-        P.bar = w.bar; P.err = w.err; P.B = B; P.n = n; P.groups = w.groups; P.g = trd_ctas_per_group(n);
+        P.bar = w.bar; P.err = w.err; P.B = B; P.n = n; P.groups = w.groups; P.g = trd_ctas_per_group(n); P.nrp = w.nrp;
         P.ldn = ldn;
-        const size_t smem = sizeof(float) * 3 * (size_t)n;
+        const size_t smem = sizeof(float) * 3 * (size_t)ldn;
         PSVD_TRY(cudaFuncSetAttribute(sytrd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int occ = 0;
         PSVD_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sytrd_kernel, kTrdThreads, smem));
@@ -556,10 +736,10 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
     // 2. eigenvalues
     double *tn = reinterpret_cast<double *>(w.S2hi);   // B doubles of scratch (S2 is free until stage 4)
     {
-        dim3 g((n + 255) / 256, B);
+        dim3 g((n + 63) / 64, B);
         const size_t smem = sizeof(float) * 2 * (size_t)n;
         PSVD_TRY(cudaFuncSetAttribute(tri_bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        tri_bisect_kernel<<<g, 256, smem, st>>>(w.d, w.e, n, w.lam, tn);
+        tri_bisect_kernel<<<g, 64, smem, st>>>(w.d, w.e, n, w.lam, tn);
         PSVD_TRY(cudaGetLastError());
         count_launch(1);
     }
@@ -574,7 +754,7 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
         P.D = w.d; P.E = w.e; P.tn = tn; P.lam = w.lam;
         P.xs = w.xs; P.u0 = w.u0; P.u1 = w.u1; P.u2 = w.u2; P.lm = w.lm; P.piv = w.piv;
         P.n = n; P.first = b0 * n; P.count = nb * n; P.stride = w.chunk;
-        tri_invit_kernel<<<(P.count + 127) / 128, 128, 0, st>>>(P);
+        tri_invit_kernel<<<(P.count + 31) / 32, 32, 0, st>>>(P);
         tri_cluster_kernel<<<nb, 256, 0, st>>>(P, bis, 1e-5);
         dim3 g((n + 31) / 32, (n + 31) / 32, nb), blk(32, 8);
         zt_store_kernel<<<g, blk, 0, st>>>(w.xs, w.chunk, n, b0, b0 * n, w.VThi, w.VTlo, ldn);
@@ -584,13 +764,24 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
     // 4. back-transform V^T = Z^T H_{n-3} ... H_0, compact-WY blocks in descending order
     if (w.nblk > 0) {
         SplitOut vo, yo;
-        vo.hi = w.Vhi; vo.lo = w.Vlo; vo.ld = ldn; vo.bstride = (long long)n * ldn;
+        const long long np = (long long)w.nrp * ldn;
+        vo.hi = w.Vhi; vo.lo = w.Vlo; vo.ld = ldn; vo.bstride = np;
         yo.hi = w.Yhi; yo.lo = w.Ylo; yo.ld = ldn; yo.bstride = (long long)n * ldn;
-        PSVD_TRY(prepare_operand(w.Vh, ldn, (long long)n * ldn, B, n, n, false, 1.f, nullptr, vo, st));
-        PSVD_TRY(prepare_operand(w.Vh, ldn, (long long)n * ldn, B, n, n, true, 1.f, nullptr, yo, st));
+        PSVD_TRY(prepare_operand(w.Vh, ldn, np, B, w.nrp, n, false, 1.f, nullptr, vo, st));
+        PSVD_TRY(prepare_operand(w.Vh, ldn, np, B, n, n, true, 1.f, nullptr, yo, st));
+        // G = Y^T Y of every WY block: blocks of kWY Householder rows as a batch
+        for (int b = 0; b < B; ++b) {
+            MatView vh = view_of(w.Vhi + b * np, kWY, n, ldn, (long long)kWY * ldn, w.nblk);
+            MatView vl = view_of(w.Vlo + b * np, kWY, n, ldn, (long long)kWY * ldn, w.nblk);
+            GemmShape s;
+            memset(&s, 0, sizeof(s));
+            s.M = kWY; s.N = kWY; s.K = n; s.prec_uniform = PREC_TF32X3; s.err = w.err;
+            EpiStore e = epi_store_plain(w.Gm + (long long)b * w.nblk * kWY * kWY, kWY, (long long)kWY * kWY, kWY, kWY);
+            PSVD_TRY(launch_gemm(nullptr, nullptr, &vh, &vl, &vh, &vl, s, w.nblk, e, st));
+        }
         const size_t smem = sizeof(float) * 2 * kWY * kWY;
         PSVD_TRY(cudaFuncSetAttribute(larft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        larft_kernel<<<dim3(w.nblk, B), 256, smem, st>>>(w.Vh, w.tau, n, ldn, w.nblk, w.Tm);
+        larft_kernel<<<dim3(w.nblk, B), 256, smem, st>>>(w.Gm, w.tau, n, w.nblk, w.Tm);
         PSVD_TRY(cudaGetLastError());
         count_launch(1);
         for (int blk = w.nblk - 1; blk >= 0; --blk) {
@@ -602,8 +793,8 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
             {
                 MatView ahi = view_of(w.VThi + r0, n, Lr, ldn, (long long)n * ldn, B);
                 MatView alo = view_of(w.VTlo + r0, n, Lr, ldn, (long long)n * ldn, B);
-                MatView bhi = view_of(w.Vhi + (long long)k0 * ldn + r0, nb, Lr, ldn, (long long)n * ldn, B);
-                MatView blo = view_of(w.Vlo + (long long)k0 * ldn + r0, nb, Lr, ldn, (long long)n * ldn, B);
+                MatView bhi = view_of(w.Vhi + (long long)k0 * ldn + r0, nb, Lr, ldn, (long long)w.nrp * ldn, B);
+                MatView blo = view_of(w.Vlo + (long long)k0 * ldn + r0, nb, Lr, ldn, (long long)w.nrp * ldn, B);
                 GemmShape s;
                 memset(&s, 0, sizeof(s));
                 s.M = n; s.N = nb; s.K = Lr; s.prec_uniform = PREC_TF32X3; s.err = w.err;

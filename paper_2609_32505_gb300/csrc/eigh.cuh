@@ -9,7 +9,7 @@ namespace psvd {
 constexpr int kWY = 128;   // reflectors per compact-WY block in the back-transform
 
 struct EighWS {
-    int B = 0, n = 0, nblk = 0, chunk = 0;
+    int B = 0, n = 0, nblk = 0, chunk = 0, nrp = 0;   // nrp: rows of Vh, padded to kWY
     long long ldn = 0;
     float *Aw = nullptr;          // working copy of H (n x n per matrix)
     float *Vh = nullptr;          // Householder vectors as rows (n x ldn), v_k[k+1] = 1
@@ -23,6 +23,7 @@ struct EighWS {
     float *S = nullptr;                        // V^T Y for one block (n x kWY)
     float *S2hi = nullptr, *S2lo = nullptr;    // S T^T split (n x kWY)
     float *Tm = nullptr;                       // [B][nblk][kWY][kWY]
+    float *Gm = nullptr;                       // [B][nblk][kWY][kWY]  Y^T Y per block
     double *xs = nullptr;                      // inverse-iteration vectors, interleaved [n][chunk]
     double *u0 = nullptr, *u1 = nullptr, *u2 = nullptr, *lm = nullptr;
     signed char *piv = nullptr;
@@ -34,19 +35,20 @@ struct EighWS {
         B = B_; n = n_; groups = groups_;
         ldn = pad_ld(n);
         nblk = n > 2 ? (n - 2 + kWY - 1) / kWY : 0;
-        const long long B64 = B, nn = (long long)n * ldn;
+        nrp = (int)round_up(n < 1 ? 1 : n, kWY);
+        const long long B64 = B, nn = (long long)n * ldn, np = (long long)nrp * ldn;
         // inverse-iteration scratch holds whole matrices: n vectors x n entries each
         chunk = n * (int)std::max<long long>(1, std::min<long long>(B64, (1LL << 24) / ((long long)n * n)));
-        Aw = cv.template take<float>(B64 * n * n);
-        Vh = cv.template take<float>(B64 * nn);
+        Aw = cv.template take<float>(B64 * n * ldn);
+        Vh = cv.template take<float>(B64 * np);
         tau = cv.template take<float>(B64 * n);
         d = cv.template take<double>(B64 * n);
         e = cv.template take<double>(B64 * n);
         lam = cv.template take<double>(B64 * n);
-        pbuf = cv.template take<float>((long long)groups * 2 * n);
-        bar = cv.template take<unsigned>(groups + 1);
-        Vhi = cv.template take<float>(B64 * nn);
-        Vlo = cv.template take<float>(B64 * nn);
+        pbuf = cv.template take<float>((long long)groups * 2 * ldn);
+        bar = cv.template take<unsigned>((long long)groups * (2 * 160 + 1) + 1);   // release + arrival flags per group
+        Vhi = cv.template take<float>(B64 * np);
+        Vlo = cv.template take<float>(B64 * np);
         Yhi = cv.template take<float>(B64 * nn);
         Ylo = cv.template take<float>(B64 * nn);
         VThi = cv.template take<float>(B64 * nn);
@@ -55,6 +57,7 @@ struct EighWS {
         S2hi = cv.template take<float>(B64 * n * kWY);
         S2lo = cv.template take<float>(B64 * n * kWY);
         Tm = cv.template take<float>(B64 * (nblk > 0 ? nblk : 1) * kWY * kWY);
+        Gm = cv.template take<float>(B64 * (nblk > 0 ? nblk : 1) * kWY * kWY);
         xs = cv.template take<double>((long long)n * chunk);
         u0 = cv.template take<double>((long long)n * chunk);
         u1 = cv.template take<double>((long long)n * chunk);

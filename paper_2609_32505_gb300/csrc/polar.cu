@@ -116,7 +116,7 @@ __global__ void schedule_fill_kernel(int B, int K, CoefTable tab, const float *l
         lo = 1.0 - c.e;
         hi = 1.0 + c.e;
     }
-    budget[b] = budget_opt > 0 ? budget_opt : greedy_steps_to(l, 0.5 * tol, K) + 3;
+    budget[b] = budget_opt > 0 ? budget_opt : greedy_steps_to(l, 0.5 * tol, K) + 5;
 }
 
 // ------------------------------------------------------------ step epilogues

@@ -174,15 +174,45 @@ __global__ void corr_x_kernel(const float *Kt, const float *S, int n, float *X, 
     Xneg[(long long)b * n * ld + (long long)i * ld + j] = tf32_round(-x);
 }
 
-__global__ void corr_f_kernel(const float *X2, const float *X, int n, long long ld, float *F, float *Ft) {
+// Second-order singular values of Sigma + K: diag(e^-X (Sigma + K) e^-X)_i =
+// sigma_i + sum_j (sigma_i + sigma_j) X_ij^2 (one warp per row).
+__global__ void sigma_refresh_kernel(const float *X, const float *S, int n, long long ld, float *Sout, float *Sout2) {
+    const int b = blockIdx.y;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const float *x = X + (long long)b * n * ld + (long long)i * ld;
+    const float *s = S + (long long)b * n;
+    const float si = s[i];
+    float acc = 0.f;
+    for (int j = lane; j < n; j += 32) acc += (si + s[j]) * x[j] * x[j];
+    acc = warp_sum(acc);
+    if (lane == 0) {
+        Sout[(long long)b * n + i] = si + acc;
+        if (Sout2) Sout2[(long long)b * n + i] = si + acc;
+    }
+}
+
+// F = X + X^2/2 - X^4/8 and Ft = -X + X^2/2 - X^4/8: (I + F)(I + F)^T = I + O(X^8), the
+// -X^4/8 term being one Newton-Schulz step on I + X + X^2/2 (whose Gram is I + X^4/4).
+__global__ void corr_f_kernel(const float *X2, const float *X4, const float *X, int n, long long ld, float *F,
+                              float *Ft) {
     const int b = blockIdx.z;
     const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
     if (i >= n || j >= n) return;
     const long long o = (long long)b * n * ld + (long long)i * ld + j;
+    const long long p = (long long)b * n * n + (long long)i * n + j;
     const float x = X[o];
-    const float h = 0.5f * X2[(long long)b * n * n + (long long)i * n + j];
+    const float h = 0.5f * X2[p] - 0.125f * X4[p];
     F[o] = tf32_round(x + h);
     Ft[o] = tf32_round(-x + h);
+}
+
+// X^2 split for the X^2 X^2 product (symmetric operand)
+__global__ void x2_split_kernel(const float *X2, int n, long long ld, float *hi) {
+    const int b = blockIdx.z;
+    const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
+    if (i >= n || j >= n) return;
+    hi[(long long)b * n * ld + (long long)i * ld + j] = tf32_round(X2[(long long)b * n * n + (long long)i * n + j]);
 }
 
 __global__ void add_split_kernel(const float *vthi, const float *vtlo, const float *FV, const float *FtV, int n,
@@ -316,11 +346,17 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
         EpiStore e2 = epi_store_plain(w.Kt, n, (long long)n * n, n, n);
         if (int rc = gemm3(w.T1hi, w.T1lo, n, n, ld, nn, vthi, vtlo, n, ld, nn, B, PREC_TF32X3, e2, p.err, st)) return rc;
         corr_x_kernel<<<g16, b16, 0, st>>>(w.Kt, w.S, n, w.X, w.Xneg, ld);
-        count_launch(1);
+        sigma_refresh_kernel<<<dim3((n + 7) / 8, B), 256, 0, st>>>(w.X, w.S, n, ld, Sout, nullptr);
+        count_launch(2);
         // X^2 = X X   (B operand B[j][k] = X[k][j] = -X[j][k])
         EpiStore e3 = epi_store_plain(w.X2, n, (long long)n * n, n, n);
         if (int rc = gemm3(w.X, nullptr, n, n, ld, nn, w.Xneg, nullptr, n, ld, nn, B, PREC_TF32, e3, p.err, st)) return rc;
-        corr_f_kernel<<<g16, b16, 0, st>>>(w.X2, w.X, n, ld, w.F, w.Ft);
+        // X^4 = X^2 X^2 (X^2 symmetric), kept in T1
+        x2_split_kernel<<<g16, b16, 0, st>>>(w.X2, n, ld, w.T1hi);
+        count_launch(1);
+        EpiStore e3b = epi_store_plain(w.T1, n, (long long)n * n, n, n);
+        if (int rc = gemm3(w.T1hi, nullptr, n, n, ld, nn, w.T1hi, nullptr, n, ld, nn, B, PREC_TF32, e3b, p.err, st)) return rc;
+        corr_f_kernel<<<g16, b16, 0, st>>>(w.X2, w.T1, w.X, n, ld, w.F, w.Ft);
         count_launch(1);
         // Ft V^T (kept split in VEt) and F V^T (in T1); B operand B[j][k] = V^T[k][j] = V[j][k]
         float *VEt_hi = w.VEt, *VEt_lo = w.VEt + (long long)B * nn;
