@@ -144,7 +144,7 @@ int psvd_polar_bwd(const float *A, const float *W, const float *H, const float *
 
 /* ---- learned schedule (the lower-bound predictor) ---------------------------
  * psvd_sketch_features -- 8 features per matrix of X0 = M / sqrt(||M||_1 ||M||_inf):
- *   Hutchinson estimates of tr(G^k)/n, k = 1..4 (G = X0^T X0) with the caller's
+ *   logs of Hutchinson estimates of tr(G^k)/n, k = 1..4 (G = X0^T X0) with the caller's
  *   Rademacher probes Z (DEVICE, batch x n x s, entries +-1), log(||X0||_F^2 / n),
  *   log(f4/f3), log(n)/10, log(m/n).  F: batch x 8 out.  ws as for svd_bwd. */
 int psvd_sketch_features(const float *A, const float *Z, int64_t s, float *F, int64_t batch,

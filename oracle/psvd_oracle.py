@@ -503,8 +503,8 @@ def ortho_error(q) -> float:
 
 def sketch_features(x0: np.ndarray, probes: np.ndarray) -> np.ndarray:
     """Eight features of the normalized matrix X0 (sigma(X0) in [0, 1]):
-    f_k = (1/(n s)) sum_probes z^T G^k z for k = 1..4 with G = X0^T X0 and the given
-    Rademacher probes z (n x s) -- Hutchinson estimates of tr(G^k)/n;
+    f_k = log( (1/(n s)) sum_probes z^T G^k z ) for k = 1..4 with G = X0^T X0 and the
+    given Rademacher probes z (n x s) -- logs of Hutchinson estimates of tr(G^k)/n;
     f_5 = log ||X0||_F^2 / n;  f_6 = log of f_4 / f_3 (ratio of power traces);
     f_7 = log(n) / 10;  f_8 = log(m / n)."""
     x0 = np.asarray(x0, dtype=np.float64)
@@ -518,7 +518,8 @@ def sketch_features(x0: np.ndarray, probes: np.ndarray) -> np.ndarray:
         t.append(float(np.sum(z * y)) / (n * s))
     fro2 = float(np.sum(x0 * x0)) / n
     tiny = 1e-30
-    return np.array([t[0], t[1], t[2], t[3],
+    lt = [math.log(max(v, tiny)) for v in t]
+    return np.array([lt[0], lt[1], lt[2], lt[3],
                      math.log(max(fro2, tiny)),
                      math.log(max(t[3], tiny) / max(t[2], tiny)),
                      math.log(n) / 10.0,

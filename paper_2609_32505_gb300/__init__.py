@@ -347,6 +347,24 @@ def mlp_train(params: torch.Tensor, feats: torch.Tensor, target: torch.Tensor, s
     return curve
 
 
+def mlp_fit(feats: torch.Tensor, target: torch.Tensor, steps: int = 2000, lr: float = 3e-3, batch: int = 256,
+            seed: int = 0):
+    """Trains the MLP with the library's Adam kernels on standardized features, then folds
+    the standardization into the first layer (W1 <- W1 / std, b1 <- b1 - W1 mean / std), so
+    the returned parameters act on raw features.  Returns (params, loss curve)."""
+    F = feats.contiguous().float()
+    mu = F.mean(0)
+    sd = F.std(0).clamp_min(1e-6)
+    params = mlp_init(seed=seed, device=F.device)
+    curve = mlp_train(params, ((F - mu) / sd).contiguous(), target, steps=steps, lr=lr, batch=batch, seed=seed)
+    w1 = params[:512].view(64, 8)
+    b1 = params[512:576]
+    w1s = w1 / sd[None, :]
+    params[576 - 64:576] = b1 - (w1s * mu[None, :]).sum(1)
+    params[:512] = w1s.flatten()
+    return params, curve
+
+
 def mlp_calibrate(params: torch.Tensor, feats: torch.Tensor, target: torch.Tensor, quantile: float = 0.98) -> float:
     """Safety margin for the predicted lower bound: exp(-q) with q the given quantile of the
     over-prediction y - target on (held-out) training data, so that about that fraction of

@@ -11,8 +11,8 @@
 
 namespace psvd {
 
-__global__ void norm_panel_kernel(const float *__restrict__ A, int m, int n, float *rowsum, float *colsum,
-                                  int *nonfinite);
+cudaError_t l1_norms(const float *A, int B, int m, int n, float *rowsum, float *colsum, int *nonfinite,
+                     cudaStream_t st);
 __global__ void norm_finalize_kernel(const float *rowsum, const float *colsum, const int *nonfinite, int m, int n,
                                      float *scale, int *done, int *status, int *fin);
 
@@ -126,7 +126,7 @@ __global__ void features_kernel(const float *acc, const float *fro, int B, int m
     float t[4];
     for (int j = 0; j < 4; ++j) t[j] = acc[b * 4 + j] * inv;
     float *f = F + (long long)b * kF;
-    f[0] = t[0]; f[1] = t[1]; f[2] = t[2]; f[3] = t[3];
+    for (int j = 0; j < 4; ++j) f[j] = logf(fmaxf(t[j], tiny));
     f[4] = logf(fmaxf(fro[b] / (float)n, tiny));
     f[5] = logf(fmaxf(t[3], tiny) / fmaxf(t[2], tiny));
     f[6] = logf((float)n) / 10.f;
@@ -258,11 +258,10 @@ extern "C" int psvd_sketch_features(const float *A, const float *Z, int64_t s, f
     PSVD_TRY(cudaMemsetAsync(w.rowsum, 0, sizeof(float) * batch * m, st));
     PSVD_TRY(cudaMemsetAsync(w.colsum, 0, sizeof(float) * batch * n, st));
     PSVD_TRY(cudaMemsetAsync(w.nonfinite, 0, sizeof(int) * batch, st));
-    norm_panel_kernel<<<dim3((Nn + 31) / 32, (M + 255) / 256, B), dim3(32, 8), 0, st>>>(A, M, Nn, w.rowsum, w.colsum,
-                                                                                          w.nonfinite);
+    PSVD_TRY(l1_norms(A, B, M, Nn, w.rowsum, w.colsum, w.nonfinite, st));
     norm_finalize_kernel<<<B, 256, 0, st>>>(w.rowsum, w.colsum, w.nonfinite, M, Nn, w.scale, w.done, w.status, w.fin);
     fro_kernel<<<B, 256, 0, st>>>(A, w.scale, (long long)m * n, w.fro);
-    count_launch(3);
+    count_launch(2);
     // Y_{j+1} = X0^T (X0 Y_j), Y_0 = Z; f_j = <Z, Y_{j+1}> / (n s)
     const float *Y = Z;
     for (int j = 0; j < 4; ++j) {

@@ -20,33 +20,45 @@
 namespace psvd {
 
 // ------------------------------------------------------------ Algorithm 2
-__global__ void norm_panel_kernel(const float *__restrict__ A, int m, int n, float *rowsum, float *colsum,
-                                  int *nonfinite) {
-    __shared__ float sh[8][33];
-    const int b = blockIdx.z;
-    const int c = blockIdx.x * 32 + threadIdx.x;
-    const int r0 = blockIdx.y * 256;
-    const float *Ab = A + (long long)b * m * n;
-    float cs = 0.f;
+// Row and column l1 norms in a fixed summation order (no atomics), so that the scale
+// and every result downstream of it are reproducible run to run.
+// rows: one warp per row; columns: one thread per column, rows in order.
+__global__ void row_l1_kernel(const float *__restrict__ A, int m, int n, float *rowsum, int *nonfinite) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.y;
+    if (warp >= m) return;
+    const float *a = A + (long long)b * m * n + (long long)warp * n;
+    float s = 0.f;
     bool bad = false;
-    for (int i = threadIdx.y; i < 256; i += 8) {
-        const int r = r0 + i;
-        if (r >= m) break;                       // uniform within the warp (one row per warp)
-        const float x = c < n ? Ab[(long long)r * n + c] : 0.f;
+    for (int j = lane; j < n; j += 32) {
+        const float x = a[j];
         bad |= !isfinite(x);
-        const float ax = fabsf(x);
-        cs += ax;
-        const float rs = warp_sum(ax);
-        if (threadIdx.x == 0) atomicAdd(&rowsum[(long long)b * m + r], rs);
+        s += fabsf(x);
     }
-    sh[threadIdx.y][threadIdx.x] = cs;
-    __syncthreads();
-    if (threadIdx.y == 0 && c < n) {
-        float t = 0.f;
-        for (int y = 0; y < 8; ++y) t += sh[y][threadIdx.x];
-        atomicAdd(&colsum[(long long)b * n + c], t);
+    s = warp_sum(s);
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+        rowsum[(long long)b * m + warp] = s;
+        if (bad) nonfinite[b] = 1;
     }
-    if (bad) nonfinite[b] = 1;
+}
+
+__global__ void col_l1_kernel(const float *__restrict__ A, int m, int n, float *colsum) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (c >= n) return;
+    const float *a = A + (long long)b * m * n + c;
+    float s = 0.f;
+    for (int i = 0; i < m; ++i) s += fabsf(a[(long long)i * n]);
+    colsum[(long long)b * n + c] = s;
+}
+
+// Launches both passes on `st`.
+cudaError_t l1_norms(const float *A, int B, int m, int n, float *rowsum, float *colsum, int *nonfinite,
+                     cudaStream_t st) {
+    row_l1_kernel<<<dim3((unsigned)(((long long)m * 32 + 255) / 256), B), 256, 0, st>>>(A, m, n, rowsum, nonfinite);
+    col_l1_kernel<<<dim3((n + 127) / 128, B), 128, 0, st>>>(A, m, n, colsum);
+    count_launch(2);
+    return cudaGetLastError();
 }
 
 // One block per matrix: s = sqrt(max col l1 * max row l1); special cases set the
@@ -420,13 +432,10 @@ int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &
     const int prec0 = w.mixed ? PREC_BF16 : PREC_TF32X3;
     polar_init_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, prec0, w.done, w.fin, w.status, w.prec, w.steps,
                                                         w.fallback);
-    {
-        dim3 g((n + 31) / 32, (m + 255) / 256, B), blk(32, 8);
-        norm_panel_kernel<<<g, blk, 0, st>>>(A, m, n, w.rowsum, w.colsum, w.nonfinite);
-    }
+    if (l1_norms(A, B, m, n, w.rowsum, w.colsum, w.nonfinite, st) != cudaSuccess) return PSVD_ERR_CUDA;
     norm_finalize_kernel<<<B, 256, 0, st>>>(w.rowsum, w.colsum, w.nonfinite, m, n, w.scale, w.done, w.status,
                                             w.fin);
-    count_launch(3);
+    count_launch(2);
     // coefficient tables: conservative CANS (Appendix B.8), classical NS, or learned bounds
     CoefTable tab;
     memset(&tab, 0, sizeof(tab));
@@ -539,3 +548,4 @@ extern "C" int psvd_polar_fwd(const float *A, float *W, float *H, int64_t batch,
     if (cv.overflow) return PSVD_ERR_WORKSPACE;
     return polar_forward(A, W, H, H != nullptr, w, o, info, static_cast<cudaStream_t>(stream));
 }
+
