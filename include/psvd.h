@@ -103,6 +103,22 @@ int psvd_polar_fwd(const float *A, float *W, float *H, int64_t batch, int64_t m,
                    const psvd_opts *opts, void *ws, size_t ws_bytes, psvd_info *info,
                    void *stream);
 
+/* psvd_polar_fwd_noalloc -- psvd_polar_fwd for callers that cannot allocate device
+ *   memory (no counterpart in the paper): code that runs while a CUDA graph is being
+ *   captured, in a real-time loop that forbids allocator calls, or under a memory
+ *   manager that owns every cudaMalloc.  Same arguments and results as psvd_polar_fwd
+ *   minus the workspace: the scratch is a fixed device array inside the library, of
+ *   psvd_polar_noalloc_capacity() bytes (64 MiB), held on every GPU that loads the
+ *   library until the process exits.  A problem whose psvd_polar_workspace_bytes exceeds
+ *   it is rejected with PSVD_ERR_WORKSPACE (psvd_last_error says so) before any work.
+ *   The first call on each device looks up the array's device address with the device
+ *   current; make that first call before capturing a stream.  Every call shares the one
+ *   array (each call clears what it needs), so calls that overlap on the GPU -- other
+ *   streams, other host threads -- race; serialize them.  Calls no cudaMalloc/cudaFree. */
+int psvd_polar_fwd_noalloc(const float *A, float *W, float *H, int64_t batch, int64_t m, int64_t n,
+                           const psvd_opts *opts, psvd_info *info, void *stream);
+size_t psvd_polar_noalloc_capacity(void);
+
 /* psvd_svd_fwd -- thin SVD M = U Sigma V^T by Algorithm 1.
  *   U: batch x m x n, S: batch x n (descending, >= 0 up to rounding), VT: batch x n x n
  *   (rows are right singular vectors; each V column's largest-|.| entry is positive).

@@ -549,3 +549,52 @@ extern "C" int psvd_polar_fwd(const float *A, float *W, float *H, int64_t batch,
     return polar_forward(A, W, H, H != nullptr, w, o, info, static_cast<cudaStream_t>(stream));
 }
 
+// ------------------------------------------------------------ allocation-free variant
+// Scratch for psvd_polar_fwd_noalloc: a fixed device array in this file, present on every
+// GPU that loads the library until the process exits.  Host code must not pass the
+// symbol itself to a kernel (on the host it names a stand-in object); its device address
+// is looked up once per device with cudaGetSymbolAddress while that device is current.
+static constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+#include <mutex>
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" size_t psvd_polar_noalloc_capacity(void) { return kNoAllocScratchBytes; }
+
+extern "C" int psvd_polar_fwd_noalloc(const float *A, float *W, float *H, int64_t batch, int64_t m, int64_t n,
+                                      const psvd_opts *opts, psvd_info *info, void *stream) {
+    psvd_opts o = resolve_opts(opts);
+    if (!A || !W || batch <= 0 || n <= 0 || m < n || batch > 65535 || !opts_ok(o)) return PSVD_ERR_ARG;
+    if ((long long)m * n > (1LL << 31)) return PSVD_ERR_ARG;
+    if (int e = check_device()) return e;
+    const size_t need = psvd_polar_workspace_bytes(batch, m, n, &o);
+    if (need > kNoAllocScratchBytes) {
+        cuda_fail(cudaErrorInvalidValue, "psvd_polar_fwd_noalloc: problem needs more scratch than the static 64 MiB",
+                  (int)(need >> 20));
+        return PSVD_ERR_WORKSPACE;
+    }
+    int dev = 0;
+    PSVD_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return PSVD_ERR_ARG;
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            PSVD_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+            g_noalloc_ptr[dev] = p;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    Carver cv(scratch, kNoAllocScratchBytes);
+    PolarWS w;
+    w.carve(cv, (int)batch, (int)m, (int)n, polar_kcap(o), o.precision == PSVD_PREC_MIXED);
+    if (cv.overflow) return PSVD_ERR_WORKSPACE;
+    return polar_forward(A, W, H, H != nullptr, w, o, info, static_cast<cudaStream_t>(stream));
+}
