@@ -229,8 +229,9 @@ def main():
     launches0 = P.kernel_launches()
     with ClockSampler(local) as clk:
         t_mixed = timed(mixed, args.steps)
+        launches = P.kernel_launches() - launches0     # over the K timed headline steps
         t_plain = timed(plain, args.steps)
-    launches = (P.kernel_launches() - launches0) // 2
+    launches_plain = P.kernel_launches() - launches0 - launches
     ms_mixed, ms_plain = float(np.mean(t_mixed)), float(np.mean(t_plain))
     if ws > 1:
         t = torch.tensor([ms_mixed, ms_plain], device=dev)
@@ -301,6 +302,8 @@ def main():
                            "path": "mixed: BF16->TF32->split-TF32 polish + eigenbasis correction, CANS delta=0.99",
                            "plain_ms": ms_plain, "speedup_mixed_vs_plain": ms_plain / ms_mixed,
                            "l2": "512 MB buffer written between timed steps",
+                           "launches_per_step": {"mixed": launches // max(1, args.steps),
+                                                 "plain": launches_plain // max(1, args.steps)},
                            "accuracy_mixed": {"sigma_err_rel_smax": sig_err, "ortho_resid": info_m["ortho_resid"],
                                               "polar_steps": [info_m["steps_bf16"], info_m["steps_tf32"],
                                                               info_m["steps_3xtf32"]]}},

@@ -1,0 +1,97 @@
+"""Per-stage timings of the SVD pipeline through the C ABI (CUDA events, after warm-up).
+
+  python -m paper_2609_32505_gb300.microbench gemm  --n 4096 --prec 0|1|2   (BF16, TF32, split-TF32)
+  python -m paper_2609_32505_gb300.microbench polar --n 4096 --prec 0|1 [--learned]
+  python -m paper_2609_32505_gb300.microbench eigh  --n 4096
+  python -m paper_2609_32505_gb300.microbench svd   --n 4096 --prec 0|1
+  python -m paper_2609_32505_gb300.microbench stages --n 4096
+
+Inputs are A = Q1 diag(s) Q2^T with s_i = kappa^((n-i)/(n-1)) (kappa = 10 by default),
+generated on the device.  `--reps 1 --warmup 1` keeps a profiler capture to a couple of
+launches of each kernel.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import paper_2609_32505_gb300 as P  # noqa: E402
+import workloads as W  # noqa: E402
+
+
+def _time(f, reps: int, warmup: int) -> float:
+    for _ in range(warmup):
+        f()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        f()
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("what", choices=["gemm", "polar", "eigh", "svd", "stages"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--m", type=int, default=0)
+    ap.add_argument("--batch", type=int, default=1)
+    ap.add_argument("--prec", type=int, default=0)
+    ap.add_argument("--kappa", type=float, default=10.0)
+    ap.add_argument("--learned", action="store_true")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=2)
+    a = ap.parse_args(argv)
+    n, m = a.n, a.m or a.n
+    dev = torch.device("cuda")
+    P.lib()
+    A = W.torch_constructed(1, m, n, W.kappa_spectrum(n, a.kappa), device=dev, batch=a.batch)
+    if a.what == "gemm":
+        g = torch.Generator(device=dev)
+        g.manual_seed(0)
+        x = torch.randn(n, n, device=dev, generator=g)
+        y = torch.randn(n, n, device=dev, generator=g)
+        ms = _time(lambda: P.gemm_tn(x, y, a.prec), a.reps, a.warmup)
+        print(f"gemm_tn n={n} prec={a.prec}: {ms:.3f} ms, {2 * n ** 3 / ms / 1e9:.1f} TFLOP/s (operand split included)")
+        return
+    o = P.make_opts(precision=a.prec)
+    if a.learned:
+        # an oracle-free stand-in for the learned bound: 0.9 sigma_min(X0), from the known
+        # spectrum (sigma_min(A) = 1) and the normalization scale the iteration reports
+        _, _, info = P.polar(A, o, want_h=False, return_info=True)
+        lb = torch.tensor([0.9 / i["scale"] for i in info], device=dev, dtype=torch.float32)
+        o = P.make_opts(precision=a.prec, schedule=P.SCHED_LEARNED, lower_bound=lb)
+    if a.what in ("polar", "stages"):
+        ms = _time(lambda: P.polar(A, o), a.reps, a.warmup)
+        _, _, info = P.polar(A, o, return_info=True)
+        i = info[0]
+        print(f"polar n={n} prec={a.prec}: {ms:.3f} ms steps bf16/tf32/3xtf32 = "
+              f"{i['steps_bf16']}/{i['steps_tf32']}/{i['steps_3xtf32']} ortho {i['ortho_resid']:.2e}", flush=True)
+    if a.what in ("eigh", "stages"):
+        _, H = P.polar(A, P.make_opts())
+        ms = _time(lambda: P.eigh(H), a.reps, a.warmup)
+        print(f"eigh n={n}: {ms:.3f} ms", flush=True)
+    if a.what in ("svd", "stages"):
+        ms = _time(lambda: P.svd_fwd(A, o), a.reps, a.warmup)
+        print(f"svd_fwd n={n} prec={a.prec}: {ms:.3f} ms", flush=True)
+        if a.what == "stages":
+            u, s, vt = P.svd_fwd(A, o)
+            g = torch.randn_like(u)
+            ms = _time(lambda: P.svd_bwd(A, u, s, vt, g, torch.ones_like(s), g.transpose(-1, -2).contiguous()),
+                       a.reps, a.warmup)
+            print(f"svd_bwd n={n}: {ms:.3f} ms", flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -145,15 +145,14 @@ def schedule_family(seed: int, n: int):
 
 
 # --------------------------------------------------------------------------
-# Device-side generation for the large workloads (same recipe, torch RNG).
-# Used where a CPU QR of the factors would take minutes; these inputs are
-# checked through properties that hold at any size (known spectrum, Weyl).
+# Large workloads (same recipe, torch RNG): the Gaussian factors and their QR are
+# made on the host in FP64 (LAPACK), the product on the device in FP64.  These
+# inputs are checked through properties that hold at any size (known spectrum, Weyl).
 # --------------------------------------------------------------------------
 
-def torch_orthonormal(gen, m: int, n: int, device, dtype=None):
+def torch_orthonormal(gen, m: int, n: int):
     import torch
-    dt = torch.float64 if dtype is None else dtype
-    g = torch.randn(m, n, generator=gen, device=device, dtype=dt)
+    g = torch.randn(m, n, generator=gen, dtype=torch.float64)
     q, r = torch.linalg.qr(g, mode="reduced")
     d = torch.sign(torch.diagonal(r))
     d = torch.where(d == 0, torch.ones_like(d), d)
@@ -161,18 +160,19 @@ def torch_orthonormal(gen, m: int, n: int, device, dtype=None):
 
 
 def torch_constructed(seed: int, m: int, n: int, s, device="cuda", batch: int = 1):
-    """Batch of A_b = Q1_b diag(s_b) Q2_b^T generated on ``device`` in FP64, returned
-    as FP32 (batch, m, n).  ``s`` is (n,) or (batch, n)."""
+    """Batch of A_b = Q1_b diag(s_b) Q2_b^T (Q from the host QR of seeded Gaussians),
+    formed on ``device`` in FP64 and returned as FP32 (batch, m, n).  ``s`` is (n,) or
+    (batch, n)."""
     import torch
-    gen = torch.Generator(device=device)
+    gen = torch.Generator()
     gen.manual_seed(int(seed))
     s = torch.as_tensor(np.asarray(s, dtype=np.float64), device=device)
     if s.dim() == 1:
         s = s[None, :].expand(batch, -1)
     out = torch.empty(batch, m, n, device=device, dtype=torch.float32)
     for b in range(batch):
-        q1 = torch_orthonormal(gen, m, n, device)
-        q2 = torch_orthonormal(gen, n, n, device)
+        q1 = torch_orthonormal(gen, m, n).to(device)
+        q2 = torch_orthonormal(gen, n, n).to(device)
         out[b] = ((q1 * s[b][None, :]) @ q2.T).float()
         del q1, q2
     return out
