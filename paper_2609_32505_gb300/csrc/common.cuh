@@ -224,6 +224,55 @@ PSVD_DEV void flag_barrier(unsigned *arrive, unsigned *release, int cig, int g, 
     __syncthreads();
 }
 
+// ---------------------------------------------------------------- float-float sums
+// Compensated FP32 accumulation (Knuth's TwoSum and the FMA-based exact product,
+// written with the _rn intrinsics so that no add is contracted into an FMA): the
+// pair (hi, lo) carries about twice the FP32 precision.  On GB300 the FP64 pipe is
+// narrow, and these sums keep long reductions on the FP32 pipe.
+struct ff { float hi, lo; };
+PSVD_DEV ff ff_zero() { return ff{0.f, 0.f}; }
+PSVD_DEV ff ff_add(ff a, ff b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    const float t = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float h = __fadd_rn(s, t);
+    return ff{h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+// a + x * y
+PSVD_DEV ff ff_fma(ff a, float x, float y) {
+    const float p = __fmul_rn(x, y);
+    const float pe = __fmaf_rn(x, y, -p);
+    const float s = __fadd_rn(a.hi, p);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    const float t = __fadd_rn(e, __fadd_rn(a.lo, pe));
+    const float h = __fadd_rn(s, t);
+    return ff{h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+PSVD_DEV ff warp_sum(ff v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ff w;
+        w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = ff_add(v, w);
+    }
+    return v;
+}
+// Block-wide sum, returned to every thread as the nearest FP32 value; `red` holds
+// 2 x 32 floats of shared memory.  Contains two __syncthreads.
+PSVD_DEV float block_sum_ff(ff v, float *red) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) { red[w] = v.hi; red[32 + w] = v.lo; }
+    __syncthreads();
+    ff t = ff_zero();
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = ff_add(t, ff{red[i], red[32 + i]});
+    return __fadd_rn(t.hi, t.lo);
+}
+
 PSVD_DEV double block_sum(double v, double *red) {
     v = warp_sum(v);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;

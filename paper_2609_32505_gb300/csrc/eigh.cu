@@ -31,69 +31,56 @@ struct TrdParams {
 
 // Householder step data: x (row k, columns > k, corrected) -> v (v[k+1] = 1), tau, beta.
 // Every CTA computes it redundantly from the same inputs, so no broadcast is needed.
-PSVD_DEV void householder_from_row(float *bx, int k, int n, double *red, float &ftau, double &beta_out) {
-    double s2 = 0.0;
-    for (int j = k + 2 + threadIdx.x; j < n; j += blockDim.x) s2 += (double)bx[j] * bx[j];
-    s2 = block_sum(s2, red);
-    const double alpha = bx[k + 1];
-    double beta, tau, scal;
-    if (s2 == 0.0) { beta = alpha; tau = 0.0; scal = 0.0; }
+// The squared norm is a compensated FP32 sum (relative error ~ u, independent of n);
+// beta, tau and the scaling follow in FP32 as in single-precision LAPACK.
+PSVD_DEV void householder_from_row(float *bx, int k, int n, float *red, float &ftau, double &beta_out) {
+    ff s2p = ff_zero();
+    for (int j = k + 2 + threadIdx.x; j < n; j += blockDim.x) s2p = ff_fma(s2p, bx[j], bx[j]);
+    const float s2 = block_sum_ff(s2p, red);
+    const float alpha = bx[k + 1];
+    float beta, tau, scal;
+    if (s2 == 0.f) { beta = alpha; tau = 0.f; scal = 0.f; }
     else {
-        beta = -copysign(sqrt(alpha * alpha + s2), alpha);
+        beta = -copysignf(sqrtf(__fmaf_rn(alpha, alpha, s2)), alpha);
         tau = (beta - alpha) / beta;
-        scal = 1.0 / (alpha - beta);
+        scal = 1.f / (alpha - beta);
     }
     __syncthreads();
-    for (int j = k + 2 + threadIdx.x; j < n; j += blockDim.x) bx[j] = (float)(bx[j] * scal);
+    for (int j = k + 2 + threadIdx.x; j < n; j += blockDim.x) bx[j] = bx[j] * scal;
     if (threadIdx.x == 0) bx[k + 1] = 1.f;
     __syncthreads();
-    ftau = (float)tau;
+    ftau = tau;
     beta_out = beta;
 }
 
-// dst[j] = src[j] for j in [jstart, n) (16-byte aligned float4 loads, all issued before
-// the stores); entries of the first partial vector below jstart are copied too.
-PSVD_DEV void load_vec4(float *dst, const float *src, int jstart, int n) {
+// Two vectors at once: d1 = s1 and d2 = s2 on the 16-byte chunks covering [jstart, n),
+// with every global load issued before the first shared-memory store; the entries
+// from n up to the end of the last chunk are zeroed.
+PSVD_DEV void load2_vec4(float *d1, const float *s1, float *d2, const float *s2, int jstart, int n) {
     const int c0 = jstart >> 2, c1 = (n + 3) >> 2;
-    const float4 *s4 = reinterpret_cast<const float4 *>(src);
-    float4 *d4 = reinterpret_cast<float4 *>(dst);
-    float4 r[4];
+    const float4 *a4 = reinterpret_cast<const float4 *>(s1), *b4 = reinterpret_cast<const float4 *>(s2);
+    float4 *x4 = reinterpret_cast<float4 *>(d1), *y4 = reinterpret_cast<float4 *>(d2);
+    float4 ra[4], rb[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int c = c0 + threadIdx.x + u * blockDim.x;
-        if (c < c1) r[u] = s4[c];
+        if (c < c1) { ra[u] = a4[c]; rb[u] = b4[c]; }
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int c = c0 + threadIdx.x + u * blockDim.x;
-        if (c < c1) d4[c] = r[u];
+        if (c < c1) { x4[c] = ra[u]; y4[c] = rb[u]; }
     }
-    for (int c = c0 + threadIdx.x + 4 * blockDim.x; c < c1; c += blockDim.x) d4[c] = s4[c];
+    for (int c = c0 + threadIdx.x + 4 * blockDim.x; c < c1; c += blockDim.x) { x4[c] = a4[c]; y4[c] = b4[c]; }
+    __syncthreads();
+    for (int j = n + threadIdx.x; j < 4 * c1; j += blockDim.x) { d1[j] = 0.f; d2[j] = 0.f; }
 }
 
-// dst[j] = row[j] - (vk w[j] + wk v[j]) for j >= jstart, 0 below (row k+1 corrected by
-// the pending rank-2 update of step k).
-PSVD_DEV void corrected_row_vec4(float *dst, const float *row, const float *v, const float *w, float vk, float wk,
-                                 int jstart, int n) {
-    const int c1 = (n + 3) >> 2;
-    const float4 *r4 = reinterpret_cast<const float4 *>(row);
-    for (int c = threadIdx.x; c < c1; c += 4 * blockDim.x) {
-        float4 r[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (c + u * (int)blockDim.x < c1 && 4 * (c + u * (int)blockDim.x) + 3 >= jstart) r[u] = r4[c + u * blockDim.x];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int cc = c + u * blockDim.x;
-            if (cc >= c1) break;
-            const float x[4] = {r[u].x, r[u].y, r[u].z, r[u].w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int j = 4 * cc + e;
-                dst[j] = (j >= jstart && j < n) ? x[e] - (vk * w[j] + wk * v[j]) : 0.f;
-            }
-        }
-    }
+// In place: x[j] -= vk w[j] + wk v[j] for j in [jstart, n) (row k+1 corrected by the
+// pending rank-2 update of step k).  Entries below jstart are left as they are and
+// never read afterwards.
+PSVD_DEV void correct_row(float *x, const float *v, const float *w, float vk, float wk, int jstart, int n) {
+    for (int j = jstart + threadIdx.x; j < n; j += blockDim.x) x[j] -= vk * w[j] + wk * v[j];
 }
 
 // One pass over an owned row i: optional rank-2 update with (u_v, u_w) on columns
@@ -163,7 +150,7 @@ PSVD_DEV float row_pass(float *Ai, int jstart, int n, const float *uv, const flo
 // accumulates the matrix-vector product of step k+1.
 __global__ void __launch_bounds__(kTrdThreads, 2) sytrd_kernel(TrdParams P) {
     extern __shared__ __align__(16) float sm[];
-    __shared__ double red[32];
+    __shared__ float red[64];
     const int n = P.n;
     const int ln = (int)P.ldn;
     float *bufs[3] = {sm, sm + ln, sm + 2 * ln};
@@ -207,27 +194,29 @@ __global__ void __launch_bounds__(kTrdThreads, 2) sytrd_kernel(TrdParams P) {
         for (int k = 0; k + 2 < n; ++k) {
             // w_k = p_k - (tau_k/2)(p_k . v_k) v_k
             const float *pb = P.pbuf + ((long long)grp * 2 + (k & 1)) * ln;
-            load_vec4(bw, pb, k + 1, n);
+            const bool more = k + 3 < n;          // a reflector k+1 exists
+            const float *Ar = A + (long long)(k + 1) * ln;
+            // p_k and the stored row k+1 travel together (row k+1 is final up to the
+            // pending update of step k, applied below)
+            load2_vec4(bw, pb, bn, Ar, k + 1, n);
             __syncthreads();
-            double pv = 0.0;
-            for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) pv += (double)bw[j] * bv[j];
-            pv = block_sum(pv, red);
-            const float K = (float)(0.5 * (double)tau_k * pv);
+            const float akk = bn[k + 1];
+            ff pvp = ff_zero();
+            for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) pvp = ff_fma(pvp, bw[j], bv[j]);
+            const float K = 0.5f * tau_k * block_sum_ff(pvp, red);
             for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) bw[j] -= K * bv[j];
             __syncthreads();
-            const bool more = k + 3 < n;          // a reflector k+1 exists
             float tau_n = 0.f;
             if (more) {
                 // row k+1 corrected by (v_k, w_k) -> reflector k+1
                 const float vk = bv[k + 1], wk = bw[k + 1];
-                const float *Ar = A + (long long)(k + 1) * ln;
-                corrected_row_vec4(bn, Ar, bv, bw, vk, wk, k + 2, n);
+                correct_row(bn, bv, bw, vk, wk, k + 2, n);
                 __syncthreads();
                 double beta;
                 householder_from_row(bn, k + 1, n, red, tau_n, beta);
                 if (cig == 0) {
                     if (threadIdx.x == 0) {
-                        D[k + 1] = (double)Ar[k + 1] - 2.0 * (double)vk * (double)wk;
+                        D[k + 1] = (double)akk - 2.0 * (double)vk * (double)wk;
                         E[k + 1] = beta;
                         P.tau[(long long)b * n + k + 1] = tau_n;
                     }
@@ -691,17 +680,6 @@ __global__ void eig_finalize_kernel(float *VThi, float *VTlo, long long ldn, int
 }
 
 // ------------------------------------------------------------ host
-static int num_sms() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
-    return sms;
-}
-
 // CTAs per matrix for the tridiagonalization (up to two per SM) and matrices in flight.
 static int trd_ctas_per_group(int n) { return std::max(1, std::min(std::min(2 * num_sms(), 320), n / 16)); }
 

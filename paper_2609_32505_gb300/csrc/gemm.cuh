@@ -6,218 +6,275 @@
 // so one well-tested kernel serves the Gram matrix, the polynomial apply, H, U and
 // the backward chain.
 //
-// Tile 128 x 128 (UMMA M = 128, N = 128, cta_group::1), accumulator in 128 TMEM
-// columns.  Each pipeline stage holds four 16 KB sub-tiles of 128 rows x 128 B,
-// each in the canonical 128-byte-swizzled K-major layout written by TMA:
-//   PREC_TF32X3 : A_hi, A_lo, B_hi, B_lo over 32 fp32 of K;   3 MMAs per k-step
-//                 (hi*hi + hi*lo + lo*hi: split-TF32, FP32-accurate products)
-//   PREC_TF32   : A[k0:32], A[k32:64], B[k0:32], B[k32:64];   1 MMA per k-step
-//   PREC_BF16   : A[k0:64], A[k64:128], B[k0:64], B[k64:128]; 1 MMA per k-step
-// Warp roles: warps 0-3 epilogue (TMEM lanes 32w..32w+31), warp 4 TMA producer,
-// warp 5 MMA issuer.  The precision is chosen per CTA at run time (per batch
-// entry), which lets the polar iteration switch precision matrix by matrix.
+// Persistent kernel: one CTA per SM walks a static list of output tiles of
+// 128 x BN (BN = 256, or 128 when N <= 128), UMMA M = 128, N = BN, cta_group::1.
+// Shared memory holds a ring of kStages units of 48 KB, each one TMA'd k-block:
+// an A sub-tile (128 rows x 128 B) and a B sub-tile (BN rows x 128 B), both in the
+// canonical 128-byte-swizzled K-major layout:
+//   PREC_BF16   : 64 bf16 of K per unit, one unit per k-block
+//   PREC_TF32   : 32 fp32 of K per unit, one unit per k-block
+//   PREC_TF32X3 : 32 fp32 of K, two units per k-block (hi parts, lo parts);
+//                 hi*hi + hi*lo + lo*hi (split-TF32, FP32-accurate products)
+// Two accumulators of 128 x 256 FP32 in TMEM (all 512 columns) let the MMA warp
+// run the next tile (or the next split-TF32 chunk) while the epilogue drains the
+// previous one.  The tensor core accumulates with truncation; split-TF32 tiles are
+// therefore flushed into round-to-nearest FP32 registers after every k-block.
+// Warp roles: warps 0-7 epilogue (warp w reads TMEM lanes 32 (w % 4) .. + 31 and
+// the column half w / 4), warp 8 TMA producer, warp 9 MMA issuer.  The precision is
+// chosen per tile at run time from the tile's batch entry, which lets the polar
+// iteration switch precision matrix by matrix.
 #pragma once
+#include <algorithm>
+#include <cstring>
+
 #include "common.cuh"
 
 namespace psvd {
 
 enum Prec : int { PREC_BF16 = 0, PREC_TF32 = 1, PREC_TF32X3 = 2 };
 
-constexpr int kBM = 128, kBN = 128;
-constexpr int kSub = 16384;             // one 128 x 128 B sub-tile
-constexpr int kStageBytes = 4 * kSub;   // 64 KB
-constexpr int kStages = 3;
-constexpr int kGemmThreads = 192;
-constexpr int kGemmSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
-constexpr int kFlushKB = 2;           // split-TF32: flush the accumulator every 2 k-blocks (K = 64)
-constexpr uint32_t kTmemCols = 512;    // 2 x 128 double-buffered accumulator + 128 cross terms
+constexpr int kBM = 128;
+constexpr int kUnitA = 16384;                  // 128 rows x 128 B
+constexpr int kUnitB = 32768;                  // up to 256 rows x 128 B
+constexpr int kUnitBytes = kUnitA + kUnitB;    // 48 KB
+constexpr int kStages = 4;
+constexpr int kEpiWarps = 8;
+constexpr int kGemmThreads = (kEpiWarps + 2) * 32;
+constexpr int kGemmSmem = kStages * kUnitBytes + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int kAccCols = 256;                  // TMEM columns per accumulator
+constexpr uint32_t kTmemCols = 512;
 
 struct GemmMaps {
-    CUtensorMap a_bf16, b_bf16;  // used when a CTA runs in PREC_BF16
+    CUtensorMap a_bf16, b_bf16;  // used by PREC_BF16 tiles
     CUtensorMap a_hi, a_lo;      // fp32 (TF32 uses a_hi only)
     CUtensorMap b_hi, b_lo;
 };
 
 struct GemmShape {
     int M, N, K;            // logical sizes
-    int tiles_m, tiles_n;   // ceil(M/128), ceil(N/128)
-    int sym;                // 1: upper-triangle tiles only (i <= j); requires A == B
+    int tiles_m, tiles_n;   // ceil(M/128), ceil(N/BN)
+    int bn;                 // 128 or 256
+    int batch;
+    int sym;                // 1: only tiles that reach the upper triangle (col >= row); requires A == B
     int prec_uniform;       // used when prec == nullptr
     const int *prec;        // [batch] per-matrix precision, or nullptr
-    const int *skip;        // [batch] nonzero = matrix finished, CTA returns at once (or nullptr)
+    const int *skip;        // [batch] nonzero = matrix finished, its tiles are skipped (or nullptr)
     unsigned *err;          // device error word
 };
 
-PSVD_DEV void sym_tile(int t, int T, int &i, int &j) {
-    // enumerate (i, j) with i <= j row by row
-    int row = 0, base = 0;
-    while (row < T && t >= base + (T - row)) { base += T - row; ++row; }
-    i = row;
-    j = row + (t - base);
+// First tile column of row ti that reaches the upper triangle.
+PSVD_DEV int sym_first_col(int ti, int bn) { return (kBM * ti) / bn; }
+
+// Tile t of one matrix -> (ti, tj).
+PSVD_DEV void tile_coords(const GemmShape &s, int t, int &ti, int &tj) {
+    if (!s.sym) { ti = t / s.tiles_n; tj = t % s.tiles_n; return; }
+    int row = 0;
+    for (;;) {
+        const int cnt = s.tiles_n - sym_first_col(row, s.bn);
+        if (t < cnt || row == s.tiles_m - 1) break;
+        t -= cnt;
+        ++row;
+    }
+    ti = row;
+    tj = sym_first_col(row, s.bn) + t;
+}
+
+PSVD_DEV int tiles_per_matrix(const GemmShape &s) {
+    if (!s.sym) return s.tiles_m * s.tiles_n;
+    int c = 0;
+    for (int r = 0; r < s.tiles_m; ++r) c += s.tiles_n - sym_first_col(r, s.bn);
+    return c;
+}
+
+// k-blocks of a tile and accumulation phases (flush points) per tile.
+PSVD_DEV int kblocks(const GemmShape &s, int prec) {
+    const int kstep = prec == PREC_BF16 ? 64 : 32;
+    return (s.K + kstep - 1) / kstep;
 }
 
 template <class Epi>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 gemm_tn_kernel(const __grid_constant__ GemmMaps maps, const GemmShape shp, Epi epi) {
-    const int b = blockIdx.z;
-    if (shp.skip && shp.skip[b]) return;           // uniform across the CTA
-    int ti, tj;
-    if (shp.sym) sym_tile(blockIdx.x, shp.tiles_m, ti, tj);
-    else { ti = blockIdx.y; tj = blockIdx.x; }
-    const int prec = shp.prec ? shp.prec[b] : shp.prec_uniform;
-
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kUnitBytes);
     uint64_t *empty = full + kStages;
-    uint64_t *acc_full = empty + kStages;      // [2] accumulator chunk complete (tcgen05.commit)
-    uint64_t *acc_empty = acc_full + 2;        // [2] accumulator chunk drained by the epilogue (4 warps)
+    uint64_t *acc_full = empty + kStages;      // [2] accumulator phase complete (tcgen05.commit)
+    uint64_t *acc_empty = acc_full + 2;        // [2] accumulator drained by the epilogue (8 warps)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
-    __shared__ int s_abort;
+    __shared__ volatile int s_abort;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-        for (int i = 0; i < 2; ++i) { mbar_init(&acc_full[i], 1); mbar_init(&acc_empty[i], 4); }
+        for (int i = 0; i < 2; ++i) { mbar_init(&acc_full[i], 1); mbar_init(&acc_empty[i], kEpiWarps); }
         fence_barrier_init();
         s_abort = 0;
     }
     if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
-    if (warp == 4 && lane == 0) {
-        tma_prefetch(prec == PREC_BF16 ? &maps.a_bf16 : &maps.a_hi);
-        tma_prefetch(prec == PREC_BF16 ? &maps.b_bf16 : &maps.b_hi);
+    if (warp == kEpiWarps && lane == 0) {
+        tma_prefetch(&maps.a_hi); tma_prefetch(&maps.b_hi);
+        tma_prefetch(&maps.a_bf16); tma_prefetch(&maps.b_bf16);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int kstep = prec == PREC_BF16 ? 128 : (prec == PREC_TF32 ? 64 : 32);
-    const int nkb = (shp.K + kstep - 1) / kstep;
-    // Split-TF32 flushes the (truncating) tensor-core accumulator into FP32
-    // registers every kFlushKB k-blocks; single-pass precisions use one chunk.
-    const int F = prec == PREC_TF32X3 ? kFlushKB : (nkb > 0 ? nkb : 1);
-    const int nq = (nkb + F - 1) / F;
-    const int row_a = ti * kBM, row_b = tj * kBN;
+    const int per = tiles_per_matrix(shp);
+    const int total = per * shp.batch;
+    const int bn = shp.bn;
+    const uint32_t unit_bytes = (uint32_t)(kUnitA + bn * 128);
 
-    if (warp == 4) {
+    if (warp == kEpiWarps) {
+        // ------------------------------------------------------------ TMA producer
         if (lane == 0) {
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb % kStages;
-                if (!mbar_wait(&empty[s], ((kb / kStages) & 1) ^ 1, shp.err)) { s_abort = 1; break; }
-                uint8_t *st = smem + s * kStageBytes;
-                mbar_arrive_expect_tx(&full[s], kStageBytes);
-                const int k0 = kb * kstep;
-                if (prec == PREC_TF32X3) {
-                    tma_load_3d(st + 0 * kSub, &maps.a_hi, &full[s], k0, row_a, b);
-                    tma_load_3d(st + 1 * kSub, &maps.a_lo, &full[s], k0, row_a, b);
-                    tma_load_3d(st + 2 * kSub, &maps.b_hi, &full[s], k0, row_b, b);
-                    tma_load_3d(st + 3 * kSub, &maps.b_lo, &full[s], k0, row_b, b);
-                } else if (prec == PREC_TF32) {
-                    tma_load_3d(st + 0 * kSub, &maps.a_hi, &full[s], k0, row_a, b);
-                    tma_load_3d(st + 1 * kSub, &maps.a_hi, &full[s], k0 + 32, row_a, b);
-                    tma_load_3d(st + 2 * kSub, &maps.b_hi, &full[s], k0, row_b, b);
-                    tma_load_3d(st + 3 * kSub, &maps.b_hi, &full[s], k0 + 32, row_b, b);
-                } else {
-                    tma_load_3d(st + 0 * kSub, &maps.a_bf16, &full[s], k0, row_a, b);
-                    tma_load_3d(st + 1 * kSub, &maps.a_bf16, &full[s], k0 + 64, row_a, b);
-                    tma_load_3d(st + 2 * kSub, &maps.b_bf16, &full[s], k0, row_b, b);
-                    tma_load_3d(st + 3 * kSub, &maps.b_bf16, &full[s], k0 + 64, row_b, b);
+            uint32_t u = 0;
+            for (int t = blockIdx.x; t < total && !s_abort; t += gridDim.x) {
+                const int b = t / per;
+                if (shp.skip && shp.skip[b]) continue;
+                int ti, tj;
+                tile_coords(shp, t % per, ti, tj);
+                const int prec = shp.prec ? shp.prec[b] : shp.prec_uniform;
+                const int nkb = kblocks(shp, prec);
+                const int row_a = ti * kBM, row_b = tj * bn;
+                for (int kb = 0; kb < nkb; ++kb) {
+                    const int nu = prec == PREC_TF32X3 ? 2 : 1;
+                    for (int h = 0; h < nu; ++h, ++u) {
+                        const int s = u % kStages;
+                        if (!mbar_wait(&empty[s], ((u / kStages) & 1) ^ 1, shp.err)) { s_abort = 1; break; }
+                        uint8_t *st = smem + s * kUnitBytes;
+                        mbar_arrive_expect_tx(&full[s], unit_bytes);
+                        const CUtensorMap *ma, *mb;
+                        int k0;
+                        if (prec == PREC_BF16) { ma = &maps.a_bf16; mb = &maps.b_bf16; k0 = kb * 64; }
+                        else if (prec == PREC_TF32) { ma = &maps.a_hi; mb = &maps.b_hi; k0 = kb * 32; }
+                        else { ma = h ? &maps.a_lo : &maps.a_hi; mb = h ? &maps.b_lo : &maps.b_hi; k0 = kb * 32; }
+                        tma_load_3d(st, ma, &full[s], k0, row_a, b);
+                        tma_load_3d(st + kUnitA, mb, &full[s], k0, row_b, b);
+                    }
+                    if (s_abort) break;
                 }
             }
         }
-    } else if (warp == 5) {
+    } else if (warp == kEpiWarps + 1) {
+        // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t id_tf32 = idesc_f32acc(kFmtTF32, kBM, kBN);
-            const uint32_t id_bf16 = idesc_f32acc(kFmtBF16, kBM, kBN);
-            const uint32_t t_small = tmem + 2 * kBN;     // split-TF32 cross terms
+            const uint32_t id_tf32 = idesc_f32acc(kFmtTF32, kBM, bn);
+            const uint32_t id_bf16 = idesc_f32acc(kFmtBF16, kBM, bn);
+            uint32_t u = 0, q = 0;
             bool ok = true;
-            for (int kb = 0; kb < nkb && ok; ++kb) {
-                const int q = kb / F, buf = q & 1;
-                const bool chunk_start = (kb % F) == 0;
-                if (chunk_start && q >= 2 && !mbar_wait(&acc_empty[buf], ((q >> 1) - 1) & 1, shp.err)) {
-                    ok = false; s_abort = 1; break;
-                }
-                const uint32_t t_big = tmem + buf * kBN;
-                const int s = kb % kStages;
-                if (!mbar_wait(&full[s], (kb / kStages) & 1, shp.err)) { ok = false; s_abort = 1; break; }
-                tc_fence_after();
-                const uint32_t sa = smem_u32(smem + s * kStageBytes);
-                if (prec == PREC_TF32X3) {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const uint64_t ahi = sdesc_k128(sa + 0 * kSub + 32 * k);
-                        const uint64_t alo = sdesc_k128(sa + 1 * kSub + 32 * k);
-                        const uint64_t bhi = sdesc_k128(sa + 2 * kSub + 32 * k);
-                        const uint64_t blo = sdesc_k128(sa + 3 * kSub + 32 * k);
-                        umma_tf32(t_small, alo, bhi, id_tf32, (kb | k) != 0);
-                        umma_tf32(t_small, ahi, blo, id_tf32, 1);
-                        umma_tf32(t_big, ahi, bhi, id_tf32, (!chunk_start) || k != 0);
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                const int b = t / per;
+                if (shp.skip && shp.skip[b]) continue;
+                const int prec = shp.prec ? shp.prec[b] : shp.prec_uniform;
+                const int nkb = kblocks(shp, prec);
+                const bool x3 = prec == PREC_TF32X3;
+                for (int kb = 0; kb < nkb && ok; ++kb) {
+                    const bool phase_start = x3 || kb == 0;
+                    const bool phase_end = x3 || kb == nkb - 1;
+                    const uint32_t buf = q & 1;
+                    if (phase_start && q >= 2 && !mbar_wait(&acc_empty[buf], ((q >> 1) - 1) & 1, shp.err)) {
+                        ok = false; break;
                     }
-                } else {
-                    const uint32_t id = prec == PREC_TF32 ? id_tf32 : id_bf16;
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
+                    const uint32_t tacc = tmem + buf * kAccCols;
+                    const int s0 = u % kStages;
+                    if (!mbar_wait(&full[s0], (u / kStages) & 1, shp.err)) { ok = false; break; }
+                    int s1 = s0;
+                    if (x3) {
+                        s1 = (u + 1) % kStages;
+                        if (!mbar_wait(&full[s1], ((u + 1) / kStages) & 1, shp.err)) { ok = false; break; }
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(smem + s0 * kUnitBytes), b0 = a0 + kUnitA;
+                    const uint32_t a1 = smem_u32(smem + s1 * kUnitBytes), b1 = a1 + kUnitA;
+                    if (x3) {
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
-                            const uint64_t ad = sdesc_k128(sa + h * kSub + 32 * k);
-                            const uint64_t bd = sdesc_k128(sa + (2 + h) * kSub + 32 * k);
-                            const uint32_t en = (!chunk_start) || h != 0 || k != 0;
-                            if (prec == PREC_TF32) umma_tf32(t_big, ad, bd, id, en);
-                            else umma_f16(t_big, ad, bd, id, en);
+                            const uint64_t ahi = sdesc_k128(a0 + 32 * k), bhi = sdesc_k128(b0 + 32 * k);
+                            const uint64_t alo = sdesc_k128(a1 + 32 * k), blo = sdesc_k128(b1 + 32 * k);
+                            umma_tf32(tacc, alo, bhi, id_tf32, k != 0);
+                            umma_tf32(tacc, ahi, blo, id_tf32, 1);
+                            umma_tf32(tacc, ahi, bhi, id_tf32, 1);
+                        }
+                        umma_commit(&empty[s0]);
+                        umma_commit(&empty[s1]);
+                        u += 2;
+                    } else {
+                        const uint32_t id = prec == PREC_TF32 ? id_tf32 : id_bf16;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const uint64_t ad = sdesc_k128(a0 + 32 * k), bd = sdesc_k128(b0 + 32 * k);
+                            const uint32_t en = (!phase_start) || k != 0;
+                            if (prec == PREC_TF32) umma_tf32(tacc, ad, bd, id, en);
+                            else umma_f16(tacc, ad, bd, id, en);
+                        }
+                        umma_commit(&empty[s0]);
+                        u += 1;
+                    }
+                    if (phase_end) { umma_commit(&acc_full[buf]); ++q; }
+                }
+            }
+            if (!ok) {
+                s_abort = 1;
+                mbar_arrive(&acc_full[0]);          // release the epilogue
+                mbar_arrive(&acc_full[1]);
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        // thread owns output row ti*128 + 32 (warp % 4) + lane and BN/2 columns
+        // starting at (warp / 4) * BN/2, kept in round-to-nearest FP32 registers
+        const int quad = warp & 3, half = warp >> 2;
+        const int ncols = bn >> 1;
+        const uint32_t lane_base = uint32_t(quad * 32) << 16;
+        uint32_t q = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x) {
+            const int b = t / per;
+            if (shp.skip && shp.skip[b]) continue;
+            int ti, tj;
+            tile_coords(shp, t % per, ti, tj);
+            const int prec = shp.prec ? shp.prec[b] : shp.prec_uniform;
+            const int nkb = kblocks(shp, prec);
+            const int nph = nkb == 0 ? 0 : (prec == PREC_TF32X3 ? nkb : 1);
+            float acc[128];
+#pragma unroll
+            for (int c = 0; c < 128; ++c) acc[c] = 0.f;
+            bool ok = true;
+            for (int ph = 0; ph < nph; ++ph, ++q) {
+                const uint32_t buf = q & 1;
+                ok = mbar_wait(&acc_full[buf], (q >> 1) & 1, shp.err) && !s_abort;
+                tc_fence_after();
+                if (ok) {
+                    const uint32_t tb = tmem + lane_base + buf * kAccCols + half * ncols;
+#pragma unroll
+                    for (int c = 0; c < 128; c += 16) {
+                        if (c < ncols) {
+                            float v[16];
+                            tmem_ld16(tb + c, v);
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) acc[c + i] += v[i];
                         }
                     }
                 }
-                umma_commit(&empty[s]);                    // frees the stage once these MMAs complete
-                if ((kb % F) == F - 1 || kb == nkb - 1) umma_commit(&acc_full[buf]);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[buf]);
+                if (!ok) break;
             }
-            if (!ok) { mbar_arrive(&acc_full[0]); mbar_arrive(&acc_full[1]); }   // release the epilogue
-        }
-    } else {
-        // epilogue: warps 0-3; thread owns output row ti*128 + threadIdx.x and keeps the
-        // 128-column accumulator in FP32 registers (round-to-nearest adds)
-        float acc[kBN];
-#pragma unroll
-        for (int c = 0; c < kBN; ++c) acc[c] = 0.f;
-        const uint32_t lane_base = uint32_t(warp * 32) << 16;
-        bool ok = true;
-        for (int q = 0; q < nq && ok; ++q) {
-            const int buf = q & 1;
-            ok = mbar_wait(&acc_full[buf], (q >> 1) & 1, shp.err) && !s_abort;
-            tc_fence_after();
-            if (ok) {
-#pragma unroll
-                for (int c = 0; c < kBN; c += 16) {
-                    float v[16];
-                    tmem_ld16(tmem + lane_base + uint32_t(buf * kBN + c), v);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) acc[c + i] += v[i];
-                }
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[buf]);
-        }
-        if (ok && prec == PREC_TF32X3 && nkb > 0) {
-            tc_fence_after();
-#pragma unroll
-            for (int c = 0; c < kBN; c += 16) {
-                float v[16];
-                tmem_ld16(tmem + lane_base + uint32_t(2 * kBN + c), v);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) acc[c + i] += v[i];
-            }
-        }
-        if (ok) {
-            const int r = row_a + threadIdx.x;
+            if (!ok) break;
+            const int r = ti * kBM + quad * 32 + lane;
+            const int cbase = tj * bn + half * ncols;
             typename Epi::Acc ea;
             epi.begin(ea);
 #pragma unroll
-            for (int c = 0; c < kBN; c += 16) {
-                float v[16];
+            for (int c = 0; c < 128; c += 16) {
+                if (c < ncols) {
+                    float v[16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = acc[c + i];
-                epi.chunk(ea, b, r, row_b + c, ti, tj, v);
+                    for (int i = 0; i < 16; ++i) v[i] = acc[c + i];
+                    epi.chunk(ea, b, r, cbase + c, ti, tj, v);
+                }
             }
             epi.finish(ea, b, ti, tj);
         }
@@ -241,12 +298,13 @@ struct MatView {
     bool bf16 = false;
 };
 
-// Encodes a TMA descriptor: box = 128 rows x 128 B (32 fp32 / 64 bf16), 128-byte
+// Encodes a TMA descriptor: box = box_rows rows x 128 B (32 fp32 / 64 bf16), 128-byte
 // swizzle, zero fill outside [cols] x [rows].  Returns false if the driver rejects it.
-bool make_tmap(CUtensorMap *out, const MatView &v);
+bool make_tmap(CUtensorMap *out, const MatView &v, int box_rows = 128);
 
 void count_launch(int n = 1);
 int cuda_fail(cudaError_t e, const char *file, int line);
+int num_sms();
 
 // Optional per-launch timing of the product kernel (CUDA events on the launching
 // stream); `flops` is the algorithmic count of the launch, `prec` its class.
@@ -254,6 +312,13 @@ void prof_begin(cudaStream_t st);
 void prof_end(cudaStream_t st, double flops, int prec);
 bool prof_on();
 
+// Host copy of the tile count (same enumeration as the device).
+inline int host_tiles_per_matrix(const GemmShape &s) {
+    if (!s.sym) return s.tiles_m * s.tiles_n;
+    int c = 0;
+    for (int r = 0; r < s.tiles_m; ++r) c += s.tiles_n - (kBM * r) / s.bn;
+    return c;
+}
 
 template <class Epi>
 cudaError_t launch_gemm(const MatView *a16, const MatView *b16, const MatView *ahi, const MatView *alo,
@@ -267,23 +332,28 @@ cudaError_t launch_gemm(const MatView *a16, const MatView *b16, const MatView *a
                                              kGemmSmem);
         if (e != cudaSuccess) { cuda_fail(e, __FILE__, __LINE__); return e; }
     }
+    shp.bn = shp.N > 128 ? 256 : 128;
     GemmMaps maps;
     memset(&maps, 0, sizeof(maps));
     // Any map that is not supplied aliases a supplied one of the same role; the
-    // kernel only dereferences the maps of the precision it runs.
-    const MatView *A32 = ahi ? ahi : alo, *B32 = bhi ? bhi : blo;
-    if ((a16 && !make_tmap(&maps.a_bf16, *a16)) || (b16 && !make_tmap(&maps.b_bf16, *b16)) ||
-        (A32 && !make_tmap(&maps.a_hi, *A32)) || (alo && !make_tmap(&maps.a_lo, *alo)) ||
-        (B32 && !make_tmap(&maps.b_hi, *B32)) || (blo && !make_tmap(&maps.b_lo, *blo))) {
+    // kernel only dereferences the maps of the precision a tile runs.
+    const MatView *Ap = ahi ? ahi : (alo ? alo : a16), *Bp = bhi ? bhi : (blo ? blo : b16);
+    if (!Ap || !Bp) {
+        cuda_fail(cudaErrorInvalidValue, "launch_gemm: missing operand", __LINE__);
+        return cudaErrorInvalidValue;
+    }
+    if (!make_tmap(&maps.a_hi, ahi ? *ahi : *Ap) || !make_tmap(&maps.a_lo, alo ? *alo : *Ap) ||
+        !make_tmap(&maps.a_bf16, a16 ? *a16 : *Ap) || !make_tmap(&maps.b_hi, bhi ? *bhi : *Bp, shp.bn) ||
+        !make_tmap(&maps.b_lo, blo ? *blo : *Bp, shp.bn) || !make_tmap(&maps.b_bf16, b16 ? *b16 : *Bp, shp.bn)) {
         cuda_fail(cudaErrorInvalidValue, "tensor map encode", __LINE__);
         return cudaErrorInvalidValue;
     }
     shp.tiles_m = (shp.M + kBM - 1) / kBM;
-    shp.tiles_n = (shp.N + kBN - 1) / kBN;
-    dim3 grid;
-    if (shp.sym) grid = dim3(shp.tiles_m * (shp.tiles_m + 1) / 2, 1, batch);
-    else grid = dim3(shp.tiles_n, shp.tiles_m, batch);
-    if (grid.x == 0 || grid.y == 0 || batch == 0) return cudaSuccess;
+    shp.tiles_n = (shp.N + shp.bn - 1) / shp.bn;
+    shp.batch = batch;
+    if (shp.tiles_m == 0 || shp.tiles_n == 0 || batch == 0) return cudaSuccess;
+    const long long total = (long long)host_tiles_per_matrix(shp) * batch;
+    const int grid = (int)std::min<long long>(total, num_sms());
     const bool prof = prof_on();
     if (prof) prof_begin(st);
     gemm_tn_kernel<Epi><<<grid, kGemmThreads, kGemmSmem, st>>>(maps, shp, epi);

@@ -138,8 +138,10 @@ PSVD_DEV void store_prec(int p, long long o, float x, __nv_bfloat16 *p16, float 
     else { float h, l; split_tf32(x, h, l); phi[o] = h; plo[o] = l; }
 }
 
-// Gram tile G = X^T X (upper tiles only): accumulates ||G - I||_F^2 and stores
-// P = c1 I + c3 G (and its mirror) in the precision of this step's apply.
+// Gram tile G = X^T X (tiles reaching the upper triangle): every entry with col >= row
+// adds to ||G - I||_F^2 (off-diagonal entries twice) and stores P = c1 I + c3 G and its
+// mirror in the precision of this step's apply; entries below the diagonal are left to
+// the tile that holds their mirror.
 struct EpiGram {
     int n, B;
     const float *coef;   // coef + k*B*2
@@ -154,21 +156,21 @@ struct EpiGram {
         if (r >= n) return;
         const int p = prec[b];
         const float c1 = coef[2 * b], c3 = coef[2 * b + 1];
-        const double w = ti == tj ? 1.0 : 2.0;
         const long long base = (long long)b * n * ldp;
         double acc = 0.0;
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             const int c = c0 + i;
             if (c >= n) break;
+            if (c < r) continue;
             const float g = v[i];
             const float d = g - (r == c ? 1.f : 0.f);
-            acc += (double)d * d;
+            acc += (r == c ? 1.0 : 2.0) * (double)d * d;
             const float pv = c3 * g + (r == c ? c1 : 0.f);
             store_prec(p, base + (long long)r * ldp + c, pv, P16, Phi, Plo);
-            if (ti != tj) store_prec(p, base + (long long)c * ldp + r, pv, P16, Phi, Plo);
+            if (c != r) store_prec(p, base + (long long)c * ldp + r, pv, P16, Phi, Plo);
         }
-        a.r += w * acc;
+        a.r += acc;
     }
     PSVD_DEV void finish(Acc &a, int b, int, int) const {
         const double s = warp_sum(a.r);

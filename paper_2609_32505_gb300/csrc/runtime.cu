@@ -65,13 +65,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-bool make_tmap(CUtensorMap *out, const MatView &v) {
+bool make_tmap(CUtensorMap *out, const MatView &v, int box_rows) {
     auto fn = encode_fn();
     if (!fn || !v.ptr) return false;
     const int esz = v.bf16 ? 2 : 4;
     cuuint64_t dims[3] = {(cuuint64_t)v.cols, (cuuint64_t)v.rows, (cuuint64_t)v.batch};
     cuuint64_t strides[2] = {(cuuint64_t)v.ld * esz, (cuuint64_t)v.bstride * esz};
-    cuuint32_t box[3] = {(cuuint32_t)(128 / esz), 128u, 1u};
+    cuuint32_t box[3] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows, 1u};
     cuuint32_t estr[3] = {1, 1, 1};
     if ((strides[0] % 16) || (strides[1] % 16) || (reinterpret_cast<uintptr_t>(v.ptr) % 16)) {
         snprintf(g_err, sizeof(g_err), "tensor map alignment: strides=(%llu,%llu) ptr=%p",
@@ -87,6 +87,19 @@ bool make_tmap(CUtensorMap *out, const MatView &v) {
                  (int)r, (unsigned long long)dims[0], (unsigned long long)dims[1], (unsigned long long)dims[2],
                  (unsigned long long)strides[0], (unsigned long long)strides[1], v.ptr);
     return r == CUDA_SUCCESS;
+}
+
+int num_sms() {
+    static int sms = 0, sms_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (sms <= 0 || sms_dev != dev) {
+        sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+        sms_dev = dev;
+    }
+    return sms;
 }
 
 int check_device() {

@@ -19,7 +19,8 @@ def _ref(a, b):
 
 @pytest.mark.parametrize("prec,rtol", [(0, 2e-2), (1, 3e-3), (2, 2e-6)])
 @pytest.mark.parametrize("batch,M,N,K", [(1, 128, 128, 32), (1, 256, 384, 512), (2, 200, 77, 300),
-                                         (3, 1, 5, 7), (1, 130, 129, 1000)])
+                                         (3, 1, 5, 7), (1, 130, 129, 1000), (2, 2048, 2048, 96),
+                                         (1, 300, 1100, 200)])
 def test_gemm_tn_parity(prec, rtol, batch, M, N, K):
     import paper_2609_32505_gb300 as P
     rng = W.rng_for(M * 7 + N * 3 + K)
