@@ -273,6 +273,27 @@ PSVD_DEV float block_sum_ff(ff v, float *red) {
     return __fadd_rn(t.hi, t.lo);
 }
 
+// Flag barrier over `g` co-resident CTAs in which every CTA polls every arrival
+// flag (no release hop): CTA c publishes arrive[c] = gen, then its threads wait
+// until all g flags have reached gen.  Bounded like flag_barrier.
+PSVD_DEV void flag_barrier_all(unsigned *arrive, int cig, int g, unsigned gen, unsigned *err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        *(volatile unsigned *)&arrive[cig] = gen;
+    }
+    for (int c = threadIdx.x; c < g; c += blockDim.x) {
+        for (uint32_t i = 0;; ++i) {
+            if (*(volatile unsigned *)&arrive[c] >= gen) break;
+            if (*(volatile unsigned *)err) break;
+            if (i > kBarrierSpin) { atomicOr(err, DEV_ERR_TIMEOUT); break; }
+            __nanosleep(20);
+        }
+    }
+    __threadfence();
+    __syncthreads();
+}
+
 PSVD_DEV double block_sum(double v, double *red) {
     v = warp_sum(v);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;

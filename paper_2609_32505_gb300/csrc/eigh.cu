@@ -3,10 +3,10 @@
 //     one group barrier per reflector; the row that the next reflector is built from
 //     is left un-updated and corrected on the fly, so the rank-2 update of step k and
 //     the matrix-vector product of step k+1 touch only rows owned by the same warp).
-//  2. Eigenvalues of T by Sturm-count bisection (FP32, on T scaled to unit norm).
+//  2. Eigenvalues of T by Sturm-count multisection (FP32, on T scaled to unit norm).
 //  3. Eigenvectors of T by inverse iteration (FP64, one thread per eigenvalue,
-//     partially pivoted tridiagonal LU), Rayleigh-quotient refinement of the shift,
-//     modified Gram-Schmidt inside clusters of close eigenvalues.
+//     partially pivoted tridiagonal LU, operands streamed through shared memory),
+//     Rayleigh quotients, modified Gram-Schmidt inside clusters of close eigenvalues.
 //  4. Back-transform V^T = Z^T Q^T with compact-WY blocks of kWY reflectors on the
 //     tcgen05 split-TF32 product kernel, then the sign convention (largest-|.| entry
 //     of each eigenvector positive).
@@ -18,7 +18,22 @@
 
 namespace psvd {
 
-constexpr int kTrdThreads = 256;
+// Launch shape of the tridiagonalization (compile-time; measured best on GB300 at
+// n = 4096: 512 threads, one CTA per SM, one CTA per 32 rows, release-flag barrier;
+// every CTA polling every flag was 30% slower).
+#ifndef PSVD_TRD_THREADS
+#define PSVD_TRD_THREADS 512
+#endif
+#ifndef PSVD_TRD_MINB
+#define PSVD_TRD_MINB 1
+#endif
+#ifndef PSVD_TRD_ROWDIV
+#define PSVD_TRD_ROWDIV 32
+#endif
+#ifndef PSVD_TRD_ALLPOLL
+#define PSVD_TRD_ALLPOLL 0
+#endif
+constexpr int kTrdThreads = PSVD_TRD_THREADS;
 struct TrdParams {
     const float *H;
     float *Aw, *Vh, *tau;
@@ -148,7 +163,7 @@ PSVD_DEV float row_pass(float *Ai, int jstart, int n, const float *uv, const flo
 // barrier of step k every CTA holds v_k and w_k, builds v_{k+1} from row k+1, and then
 // makes one pass over its owned rows that applies the rank-2 update of step k and
 // accumulates the matrix-vector product of step k+1.
-__global__ void __launch_bounds__(kTrdThreads, 2) sytrd_kernel(TrdParams P) {
+__global__ void __launch_bounds__(kTrdThreads, PSVD_TRD_MINB) sytrd_kernel(TrdParams P) {
     extern __shared__ __align__(16) float sm[];
     __shared__ float red[64];
     const int n = P.n;
@@ -161,7 +176,11 @@ __global__ void __launch_bounds__(kTrdThreads, 2) sytrd_kernel(TrdParams P) {
     unsigned *rel = P.bar + (long long)grp * (P.g + 1);
     unsigned *arr = rel + 1;
     unsigned nbar = 0;
+#if PSVD_TRD_ALLPOLL
+#define TRD_BARRIER() flag_barrier_all(arr, cig, P.g, ++nbar, P.err)
+#else
 #define TRD_BARRIER() flag_barrier(arr, rel, cig, P.g, ++nbar, P.err)
+#endif
     for (int b = grp; b < P.B; b += P.groups) {
         const float *Hb = P.H + (long long)b * n * n;
         float *A = P.Aw + (long long)b * n * ln;
@@ -319,20 +338,36 @@ __global__ void tri_bisect_kernel(const double *D, const double *E, int n, doubl
     glo = FLT_MAX; ghi = -FLT_MAX;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { glo = fminf(glo, sh_lo[i]); ghi = fmaxf(ghi, sh_hi[i]); }
     if (blockIdx.x == 0 && threadIdx.x == 0 && tnorm_out) tnorm_out[b] = tn;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;   // descending index
-    if (i >= n) return;
-    if (tn == 0.0) { lam[(long long)b * n + i] = 0.0; return; }
+    // 9-way multisection: the 8 lanes of a group evaluate the Sturm count at the 8
+    // interior points of [lo, hi]; the counts are non-decreasing in x, so the lanes whose
+    // count is <= j form a prefix and its length selects the next interval.
+    const int grp = threadIdx.x >> 3, l = threadIdx.x & 7;
+    const int i = blockIdx.x * (blockDim.x >> 3) + grp;   // descending index
+    const bool valid = i < n;
     const int j = n - 1 - i;
     const float pivmin = 1e-30f;
     const float pad = 4.f * FLT_EPSILON * n + 1e-30f;
     float lo = glo - pad, hi = ghi + pad;
-    for (int it = 0; it < 80; ++it) {
-        const float mid = 0.5f * (lo + hi);
-        if (mid <= lo || mid >= hi) break;
-        if (hi - lo <= 2.f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi)) + 2e-30f) break;
-        if (sturm_count(d, e2, n, mid, pivmin) <= j) lo = mid;
-        else hi = mid;
+    const unsigned gshift = (threadIdx.x & 31) & ~7u;
+    bool stalled = false;
+    for (int round = 0; round < 24; ++round) {
+        const bool active = valid && tn > 0.0 && !stalled &&
+                            hi - lo > 2.f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi)) + 2e-30f;
+        if (!__any_sync(0xffffffffu, active)) break;
+        const float w = hi - lo;
+        const float x = lo + w * ((float)(l + 1) * (1.f / 9.f));
+        const bool le = active && sturm_count(d, e2, n, x, pivmin) <= j;
+        const unsigned bits = (__ballot_sync(0xffffffffu, le) >> gshift) & 0xFFu;
+        if (active) {
+            const int k = __popc(bits);
+            const float nlo = k > 0 ? lo + w * ((float)k * (1.f / 9.f)) : lo;
+            const float nhi = k < 8 ? lo + w * ((float)(k + 1) * (1.f / 9.f)) : hi;
+            if (nlo <= lo && nhi >= hi) stalled = true;   // no progress at float resolution
+            else { lo = nlo; hi = nhi; }
+        }
     }
+    if (!valid || l != 0) return;
+    if (tn == 0.0) { lam[(long long)b * n + i] = 0.0; return; }
     lam[(long long)b * n + i] = 0.5 * ((double)lo + (double)hi) * tn;
 }
 
@@ -347,115 +382,175 @@ struct InvitParams {
     const double *D, *E, *tn;
     double *lam;
     double *xs, *u0, *u1, *u2, *lm;
-    signed char *piv;
+    unsigned *piv;           // pivot flags, bit (j % 32) of word [j / 32][t]
     int n, first, count;     // vectors [first, first + count) of the flattened (b, i) index
     long long stride;        // = chunk
 };
 
-// factor T - mu I = P L U (U with two superdiagonals)
-PSVD_DEV void tri_factor(const InvitParams &P, const double *D, const double *E, int n, double mu, double tiny,
-                         int t) {
+// Each thread owns one eigenvector and walks its length-n recurrences in order.  The
+// operands of every pass are streamed through a per-warp shared-memory ring with
+// cp.async (kIvR stages of kIvJ rows, up to kIvNA arrays), so a warp keeps about
+// (kIvR - 1) kIvJ rows of loads in flight instead of waiting on each one.
+constexpr int kIvJ = 16, kIvR = 4, kIvNA = 4;
+constexpr int kIvStage = kIvNA * kIvJ * 32;                       // doubles per stage
+constexpr size_t kIvSmem = sizeof(double) * kIvR * kIvStage;      // 64 KB per warp
+
+PSVD_DEV void cp_async8(double *sdst, const double *gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+}
+PSVD_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+PSVD_DEV void cp_async_wait_ring() { asm volatile("cp.async.wait_group %0;" ::"n"(kIvR - 2) : "memory"); }
+
+// Streams `nsteps` rows: addr(k, a) gives the global address of array a at step k (or
+// nullptr), body(k, ring slot pointer) consumes them in order; slot(a) = p + a*kIvJ*32.
+template <class Addr, class Body>
+PSVD_DEV void iv_stream(double *ring, int nsteps, int na, Addr addr, Body body) {
+    const int lane = threadIdx.x & 31;
+    const int nst = (nsteps + kIvJ - 1) / kIvJ;
+    auto issue = [&](int st) {
+        if (st < nst) {
+            double *buf = ring + (st % kIvR) * kIvStage;
+            for (int jj = 0; jj < kIvJ; ++jj) {
+                const int k = st * kIvJ + jj;
+                if (k >= nsteps) break;
+                for (int a = 0; a < na; ++a) {
+                    const double *g = addr(k, a);
+                    if (g) cp_async8(buf + (a * kIvJ + jj) * 32 + lane, g);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    for (int st = 0; st < kIvR - 1; ++st) issue(st);
+    for (int st = 0; st < nst; ++st) {
+        cp_async_wait_ring();
+        const double *buf = ring + (st % kIvR) * kIvStage + lane;
+        for (int jj = 0; jj < kIvJ; ++jj) {
+            const int k = st * kIvJ + jj;
+            if (k >= nsteps) break;
+            body(k, buf + jj * 32);
+        }
+        issue(st + kIvR - 1);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __threadfence_block();   // this pass's stores before the next pass's async reads
+}
+#define IV_SLOT(p, a) (p)[(a) * kIvJ * 32]
+
+PSVD_DEV double iv_start(int i, int j) { return hash_unit((unsigned)i, (unsigned)j) + 0.0625; }
+
+// Factor T - mu I = P L U (U with two superdiagonals, reciprocal pivots in u0).
+PSVD_DEV void iv_factor(const InvitParams &P, double *ring, const double *D, const double *E, int n, double mu,
+                        double tiny, int t) {
     const long long s = P.stride;
     double a = D[0] - mu;
-    double bsup = n > 1 ? E[0] : 0.0;
-    for (int j = 0; j < n - 1; ++j) {
-        const double c = E[j];
-        const double dn = D[j + 1] - mu;
-        const double en = j + 1 < n - 1 ? E[j + 1] : 0.0;
-        if (fabs(a) >= fabs(c)) {
-            if (fabs(a) < tiny) a = a < 0 ? -tiny : tiny;
-            const double ra = 1.0 / a;
-            const double m = c * ra;
-            P.u0[j * s + t] = ra; P.u1[j * s + t] = bsup; P.u2[j * s + t] = 0.0; P.lm[j * s + t] = m;
-            P.piv[j * s + t] = 0;
-            a = dn - m * bsup;
-            bsup = en;
-        } else {
-            const double rc = 1.0 / c;
-            const double m = a * rc;
-            P.u0[j * s + t] = rc; P.u1[j * s + t] = dn; P.u2[j * s + t] = en; P.lm[j * s + t] = m;
-            P.piv[j * s + t] = 1;
-            a = bsup - m * dn;
-            bsup = -m * en;
-        }
-    }
+    double bsup = E[0];
+    unsigned word = 0;
+    iv_stream(ring, n - 1, 3,
+              [&](int j, int q) -> const double * {
+                  return q == 0 ? D + j + 1 : (q == 1 ? E + j : (j + 1 < n - 1 ? E + j + 1 : nullptr));
+              },
+              [&](int j, const double *p) {
+                  const double c = IV_SLOT(p, 1);
+                  const double dn = IV_SLOT(p, 0) - mu;
+                  const double en = j + 1 < n - 1 ? IV_SLOT(p, 2) : 0.0;
+                  const long long o = (long long)j * s + t;
+                  if (fabs(a) >= fabs(c)) {
+                      if (fabs(a) < tiny) a = a < 0 ? -tiny : tiny;
+                      const double ra = 1.0 / a;
+                      const double m = c * ra;
+                      P.u0[o] = ra; P.u1[o] = bsup; P.u2[o] = 0.0; P.lm[o] = m;
+                      a = dn - m * bsup;
+                      bsup = en;
+                  } else {
+                      const double rc = 1.0 / c;
+                      const double m = a * rc;
+                      P.u0[o] = rc; P.u1[o] = dn; P.u2[o] = en; P.lm[o] = m;
+                      word |= 1u << (j & 31);
+                      a = bsup - m * dn;
+                      bsup = -m * en;
+                  }
+                  if ((j & 31) == 31 || j == n - 2) { P.piv[(long long)(j >> 5) * s + t] = word; word = 0; }
+              });
     if (fabs(a) < tiny) a = a < 0 ? -tiny : tiny;
-    P.u0[(long long)(n - 1) * s + t] = 1.0 / a;     // u0 holds reciprocal pivots
+    P.u0[(long long)(n - 1) * s + t] = 1.0 / a;
 }
 
-// Solves (T - mu I) x = b in place with the stored factorization and normalizes x.
-// The loops carry one or two scalars; every load is issued kPf iterations ahead.
-PSVD_DEV void tri_solve_normalize(const InvitParams &P, int n, int t) {
-    constexpr int kPf = 8;
+// Forward part of one solve: x <- P-and-L applied to b, where b = scale * x, or the
+// start vector when `first`.
+PSVD_DEV void iv_forward(const InvitParams &P, double *ring, int n, int t, int i, bool first, double scale) {
     const long long s = P.stride;
-    double *__restrict__ x = P.xs;
-    const double *__restrict__ lm = P.lm;
-    const double *__restrict__ u0 = P.u0;
-    const double *__restrict__ u1 = P.u1;
-    const double *__restrict__ u2 = P.u2;
-    const signed char *__restrict__ pv = P.piv;
-    // forward: apply the row swaps and multipliers
-    double carry = x[t];
-    for (int j0 = 0; j0 < n - 1; j0 += kPf) {
-        double bx[kPf], bl[kPf];
-        signed char bp[kPf];
-#pragma unroll
-        for (int u = 0; u < kPf; ++u) {
-            const int j = j0 + u;
-            if (j < n - 1) { bx[u] = x[(j + 1) * s + t]; bl[u] = lm[j * s + t]; bp[u] = pv[j * s + t]; }
-        }
-#pragma unroll
-        for (int u = 0; u < kPf; ++u) {
-            const int j = j0 + u;
-            if (j < n - 1) {
-                double a = carry, b = bx[u];
-                if (bp[u]) { const double tmp = a; a = b; b = tmp; }
-                x[j * s + t] = a;
-                carry = b - bl[u] * a;
-            }
-        }
-    }
+    double *x = P.xs;
+    double carry = first ? iv_start(i, 0) : x[t] * scale;
+    unsigned pword = 0;
+    unsigned pnext = P.piv[t];
+    iv_stream(ring, n - 1, 2,
+              [&](int j, int q) -> const double * {
+                  return q == 0 ? (first ? nullptr : x + (long long)(j + 1) * s + t) : P.lm + (long long)j * s + t;
+              },
+              [&](int j, const double *p) {
+                  if ((j & 31) == 0) {
+                      pword = pnext;
+                      const long long nw = (long long)((j >> 5) + 1);
+                      if ((nw << 5) < n - 1) pnext = P.piv[nw * s + t];
+                  }
+                  double a = carry;
+                  double b = first ? iv_start(i, j + 1) : IV_SLOT(p, 0) * scale;
+                  if ((pword >> (j & 31)) & 1u) { const double tmp = a; a = b; b = tmp; }
+                  x[(long long)j * s + t] = a;
+                  carry = b - IV_SLOT(p, 1) * a;
+              });
     x[(long long)(n - 1) * s + t] = carry;
-    // backward: U x = y with reciprocal pivots in u0
-    double x1 = carry * u0[(long long)(n - 1) * s + t], x2 = 0.0;
-    x[(long long)(n - 1) * s + t] = x1;
-    double nrm = x1 * x1;
-    for (int j0 = n - 2; j0 >= 0; j0 -= kPf) {
-        double by[kPf], b0[kPf], b1[kPf], b2[kPf];
-#pragma unroll
-        for (int u = 0; u < kPf; ++u) {
-            const int j = j0 - u;
-            if (j >= 0) { by[u] = x[j * s + t]; b0[u] = u0[j * s + t]; b1[u] = u1[j * s + t]; b2[u] = u2[j * s + t]; }
-        }
-#pragma unroll
-        for (int u = 0; u < kPf; ++u) {
-            const int j = j0 - u;
-            if (j >= 0) {
-                const double v = (by[u] - b1[u] * x1 - b2[u] * x2) * b0[u];
-                x[j * s + t] = v;
-                x2 = x1;
-                x1 = v;
-                nrm += v * v;
-            }
-        }
-    }
-    const double inv = nrm > 0 ? 1.0 / sqrt(nrm) : 0.0;
-    for (int j = 0; j < n; ++j) x[j * s + t] *= inv;
 }
 
-PSVD_DEV double tri_rayleigh(const InvitParams &P, const double *D, const double *E, int n, int t) {
+// Backward part: U x = y in place; returns ||x||^2.
+PSVD_DEV double iv_backward(const InvitParams &P, double *ring, int n, int t) {
     const long long s = P.stride;
+    double *x = P.xs;
+    const long long last = (long long)(n - 1) * s + t;
+    double x1 = x[last] * P.u0[last], x2 = 0.0;
+    x[last] = x1;
+    double nrm = x1 * x1;
+    iv_stream(ring, n - 1, 4,
+              [&](int k, int q) -> const double * {
+                  const long long o = (long long)(n - 2 - k) * s + t;
+                  return q == 0 ? x + o : (q == 1 ? P.u0 + o : (q == 2 ? P.u1 + o : P.u2 + o));
+              },
+              [&](int k, const double *p) {
+                  const double v = (IV_SLOT(p, 0) - IV_SLOT(p, 2) * x1 - IV_SLOT(p, 3) * x2) * IV_SLOT(p, 1);
+                  x[(long long)(n - 2 - k) * s + t] = v;
+                  x2 = x1;
+                  x1 = v;
+                  nrm += v * v;
+              });
+    return nrm;
+}
+
+// x <- scale * x and the Rayleigh quotient x^T T x of the scaled vector.
+PSVD_DEV double iv_finish(const InvitParams &P, double *ring, const double *D, const double *E, int n, int t,
+                          double scale) {
+    const long long s = P.stride;
+    double *x = P.xs;
     double r = 0.0, prev = 0.0;
-    for (int j = 0; j < n; ++j) {
-        const double xj = P.xs[j * s + t];
-        r += D[j] * xj * xj;
-        if (j > 0) r += 2.0 * E[j - 1] * prev * xj;
-        prev = xj;
-    }
+    iv_stream(ring, n, 3,
+              [&](int j, int q) -> const double * {
+                  return q == 0 ? x + (long long)j * s + t : (q == 1 ? D + j : (j > 0 ? E + j - 1 : nullptr));
+              },
+              [&](int j, const double *p) {
+                  const double xj = IV_SLOT(p, 0) * scale;
+                  x[(long long)j * s + t] = xj;
+                  r += IV_SLOT(p, 1) * xj * xj;
+                  if (j > 0) r += 2.0 * IV_SLOT(p, 2) * prev * xj;
+                  prev = xj;
+              });
     return r;
 }
 
-__global__ void tri_invit_kernel(InvitParams P) {
+// One warp per block: 32 eigenvectors, each by inverse iteration from a fixed
+// pseudo-random start.  The bisection shift is accurate to ~1e-7 ||T||: three solves
+// reduce the other components by (shift error / gap)^3.
+__global__ void __launch_bounds__(32) tri_invit_kernel(InvitParams P) {
+    extern __shared__ __align__(16) double ivring[];
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= P.count) return;
     const int n = P.n;
@@ -463,7 +558,7 @@ __global__ void tri_invit_kernel(InvitParams P) {
     const int b = (int)(gi / n), i = (int)(gi % n);
     const double *D = P.D + (long long)b * n, *E = P.E + (long long)b * n;
     const double tn = P.tn[b];
-    double mu = P.lam[gi];
+    const double mu = P.lam[gi];
     const long long s = P.stride;
     if (n == 1) { P.xs[t] = 1.0; return; }
     if (!(tn > 0.0)) {
@@ -473,14 +568,14 @@ __global__ void tri_invit_kernel(InvitParams P) {
         return;
     }
     const double tiny = fmax(tn * 2.2e-16, 1e-280);
-    for (int j = 0; j < n; ++j) P.xs[j * s + t] = hash_unit((unsigned)i, (unsigned)j) + 0.0625;
-    // the bisection shift is accurate to ~1e-7 ||T||: three solves reduce the other
-    // components by (shift error / gap)^3
-    tri_factor(P, D, E, n, mu, tiny, t);
-    tri_solve_normalize(P, n, t);
-    tri_solve_normalize(P, n, t);
-    tri_solve_normalize(P, n, t);
-    P.lam[gi] = tri_rayleigh(P, D, E, n, t);
+    iv_factor(P, ivring, D, E, n, mu, tiny, t);
+    double scale = 1.0;
+    for (int it = 0; it < 3; ++it) {
+        iv_forward(P, ivring, n, t, i, it == 0, scale);
+        const double nrm = iv_backward(P, ivring, n, t);
+        scale = nrm > 0 ? 1.0 / sqrt(nrm) : 0.0;
+    }
+    P.lam[gi] = iv_finish(P, ivring, D, E, n, t, scale);
 }
 
 // Modified Gram-Schmidt inside clusters of eigenvalues closer than ctol * ||T||,
@@ -680,12 +775,14 @@ __global__ void eig_finalize_kernel(float *VThi, float *VTlo, long long ldn, int
 }
 
 // ------------------------------------------------------------ host
-// CTAs per matrix for the tridiagonalization (up to two per SM) and matrices in flight.
-static int trd_ctas_per_group(int n) { return std::max(1, std::min(std::min(2 * num_sms(), 320), n / 16)); }
+// CTAs per matrix for the tridiagonalization and matrices in flight.
+static int trd_ctas_per_group(int n) {
+    return std::max(1, std::min(std::min(PSVD_TRD_MINB * num_sms(), 320), n / PSVD_TRD_ROWDIV));
+}
 
 int eigh_groups(int B, int n) {
     const int g = trd_ctas_per_group(n);
-    return std::max(1, std::min(B, (2 * num_sms()) / g));
+    return std::max(1, std::min(B, (PSVD_TRD_MINB * num_sms()) / g));
 }
 
 int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t st) {
@@ -714,10 +811,10 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
     // 2. eigenvalues
     double *tn = reinterpret_cast<double *>(w.S2hi);   // B doubles of scratch (S2 is free until stage 4)
     {
-        dim3 g((n + 63) / 64, B);
+        dim3 g((n + 31) / 32, B);       // 32 eigenvalues x 8 lanes per block
         const size_t smem = sizeof(float) * 2 * (size_t)n;
         PSVD_TRY(cudaFuncSetAttribute(tri_bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        tri_bisect_kernel<<<g, 64, smem, st>>>(w.d, w.e, n, w.lam, tn);
+        tri_bisect_kernel<<<g, 256, smem, st>>>(w.d, w.e, n, w.lam, tn);
         PSVD_TRY(cudaGetLastError());
         count_launch(1);
     }
@@ -725,6 +822,7 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
     double *bis = reinterpret_cast<double *>(w.S);   // B*n doubles (S holds B*n*kWY floats)
     PSVD_TRY(cudaMemcpyAsync(bis, w.lam, sizeof(double) * (size_t)B * n, cudaMemcpyDeviceToDevice, st));
     // 3. eigenvectors of T, chunk by chunk (chunks hold whole matrices)
+    PSVD_TRY(cudaFuncSetAttribute(tri_invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIvSmem));
     const int per = std::max(1, w.chunk / n);
     for (int b0 = 0; b0 < B; b0 += per) {
         const int nb = std::min(per, B - b0);
@@ -732,7 +830,7 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
         P.D = w.d; P.E = w.e; P.tn = tn; P.lam = w.lam;
         P.xs = w.xs; P.u0 = w.u0; P.u1 = w.u1; P.u2 = w.u2; P.lm = w.lm; P.piv = w.piv;
         P.n = n; P.first = b0 * n; P.count = nb * n; P.stride = w.chunk;
-        tri_invit_kernel<<<(P.count + 31) / 32, 32, 0, st>>>(P);
+        tri_invit_kernel<<<(P.count + 31) / 32, 32, kIvSmem, st>>>(P);
         tri_cluster_kernel<<<nb, 256, 0, st>>>(P, bis, 1e-5);
         dim3 g((n + 31) / 32, (n + 31) / 32, nb), blk(32, 8);
         zt_store_kernel<<<g, blk, 0, st>>>(w.xs, w.chunk, n, b0, b0 * n, w.VThi, w.VTlo, ldn);

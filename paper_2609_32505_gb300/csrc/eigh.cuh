@@ -26,7 +26,7 @@ struct EighWS {
     float *Gm = nullptr;                       // [B][nblk][kWY][kWY]  Y^T Y per block
     double *xs = nullptr;                      // inverse-iteration vectors, interleaved [n][chunk]
     double *u0 = nullptr, *u1 = nullptr, *u2 = nullptr, *lm = nullptr;
-    signed char *piv = nullptr;
+    unsigned *piv = nullptr;            // pivot bits, [ceil(n/32)][chunk]
     unsigned *err = nullptr;
     int groups = 0;
 
@@ -63,7 +63,7 @@ struct EighWS {
         u1 = cv.template take<double>((long long)n * chunk);
         u2 = cv.template take<double>((long long)n * chunk);
         lm = cv.template take<double>((long long)n * chunk);
-        piv = cv.template take<signed char>((long long)n * chunk);
+        piv = cv.template take<unsigned>((long long)((n + 31) / 32) * chunk);
         err = cv.template take<unsigned>(4);
     }
 };
