@@ -268,8 +268,10 @@ PSVD_DEV float block_sum_ff(ff v, float *red) {
     __syncthreads();
     if (l == 0) { red[w] = v.hi; red[32 + w] = v.lo; }
     __syncthreads();
-    ff t = ff_zero();
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = ff_add(t, ff{red[i], red[32 + i]});
+    // every warp reduces the per-warp partials the same way (same result everywhere)
+    const int nw = (int)(blockDim.x >> 5);
+    ff t = l < nw ? ff{red[l], red[32 + l]} : ff_zero();
+    t = warp_sum(t);
     return __fadd_rn(t.hi, t.lo);
 }
 

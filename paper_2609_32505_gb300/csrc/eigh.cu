@@ -18,9 +18,12 @@
 
 namespace psvd {
 
-// Launch shape of the tridiagonalization (compile-time; measured best on GB300 at
-// n = 4096: 512 threads, one CTA per SM, one CTA per 32 rows, release-flag barrier;
-// every CTA polling every flag was 30% slower).
+// Launch shape of the tridiagonalization (compile-time; measured on GB300 at n = 4096:
+// 512 threads and one CTA per SM beat 256 x 2; the release-flag barrier with short
+// sleeps between polls beat both every CTA polling every flag (30% slower) and polling
+// without sleeps (7% slower: the pollers contend for the flag's L2 line)).  The per-step row pass moves the trailing matrix
+// through L2 twice, so it is bound by SM-L2 bandwidth: use every SM once the matrix
+// has enough rows (one CTA per 24 rows).
 #ifndef PSVD_TRD_THREADS
 #define PSVD_TRD_THREADS 512
 #endif
@@ -28,10 +31,10 @@ namespace psvd {
 #define PSVD_TRD_MINB 1
 #endif
 #ifndef PSVD_TRD_ROWDIV
-#define PSVD_TRD_ROWDIV 32
+#define PSVD_TRD_ROWDIV 24
 #endif
-#ifndef PSVD_TRD_ALLPOLL
-#define PSVD_TRD_ALLPOLL 0
+#ifndef PSVD_TRD_BARRIER
+#define PSVD_TRD_BARRIER 0      // 0: release flag, 1: every CTA polls every flag
 #endif
 constexpr int kTrdThreads = PSVD_TRD_THREADS;
 struct TrdParams {
@@ -172,11 +175,13 @@ __global__ void __launch_bounds__(kTrdThreads, PSVD_TRD_MINB) sytrd_kernel(TrdPa
     const int grp = blockIdx.x / P.g, cig = blockIdx.x % P.g;
     if (grp >= P.groups) return;
     const int nwarp = kTrdThreads / 32, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gw = cig * nwarp + warp, GW = P.g * nwarp;
+    // rows go to warps warp-major across the CTAs (row i -> CTA i % g), so every CTA owns
+    // about n / g rows spread over the whole matrix and loses them at the same rate
+    const int gw = warp * P.g + cig, GW = P.g * nwarp;
     unsigned *rel = P.bar + (long long)grp * (P.g + 1);
     unsigned *arr = rel + 1;
     unsigned nbar = 0;
-#if PSVD_TRD_ALLPOLL
+#if PSVD_TRD_BARRIER == 1
 #define TRD_BARRIER() flag_barrier_all(arr, cig, P.g, ++nbar, P.err)
 #else
 #define TRD_BARRIER() flag_barrier(arr, rel, cig, P.g, ++nbar, P.err)
@@ -233,7 +238,7 @@ __global__ void __launch_bounds__(kTrdThreads, PSVD_TRD_MINB) sytrd_kernel(TrdPa
                 __syncthreads();
                 double beta;
                 householder_from_row(bn, k + 1, n, red, tau_n, beta);
-                if (cig == 0) {
+                if (cig == (k + 1) % P.g) {     // the CTAs take turns storing the reflector
                     if (threadIdx.x == 0) {
                         D[k + 1] = (double)akk - 2.0 * (double)vk * (double)wk;
                         E[k + 1] = beta;
