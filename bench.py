@@ -191,7 +191,7 @@ def main():
         S = torch.empty(1, N, device=dev)
         VT = torch.empty(1, N, N, device=dev)
         dA = torch.empty(1, N, N, device=dev)
-        info = torch.zeros(1, 9, dtype=torch.int32, device=dev)
+        info = torch.zeros(1, P.INFO_WORDS, dtype=torch.int32, device=dev)
         wsf = P._workspace(L.psvd_svd_workspace_bytes(1, N, N, ctypes.byref(o)), dev)
         wsb = P._workspace(L.psvd_svd_bwd_workspace_bytes(1, N, N), dev)
         return o, U, S, VT, dA, info, wsf, wsb
@@ -204,20 +204,17 @@ def main():
         P._check(L.psvd_svd_bwd(P._ptr(a_dev), P._ptr(U), P._ptr(S), P._ptr(VT), P._ptr(GU), P._ptr(GS),
                                 P._ptr(GVT), P._ptr(dA), 1, N, N, EPS, 0, P._ptr(wsb), wsb.numel(), st), "svd_bwd")
 
-    def timed(bufs, steps):
-        times = []
-        for _ in range(steps):
-            flush.fill_(1.0)
-            torch.cuda.synchronize()
-            if ws > 1:
-                torch.distributed.barrier()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            step(bufs, A)
-            e1.record()
-            torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
-        return times
+    def timed_one(bufs):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step(bufs, A)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
 
     mixed = make(P.PREC_MIXED)
     plain = make(P.PREC_FP32)
@@ -226,12 +223,17 @@ def main():
         step(plain, A)
     torch.cuda.synchronize()
 
-    launches0 = P.kernel_launches()
+    # the two paths alternate step by step, so that both see the same clocks and box state
+    t_mixed, t_plain = [], []
+    launches = launches_plain = 0
     with ClockSampler(local) as clk:
-        t_mixed = timed(mixed, args.steps)
-        launches = P.kernel_launches() - launches0     # over the K timed headline steps
-        t_plain = timed(plain, args.steps)
-    launches_plain = P.kernel_launches() - launches0 - launches
+        for _ in range(args.steps):
+            c0 = P.kernel_launches()
+            t_mixed.append(timed_one(mixed))
+            c1 = P.kernel_launches()
+            t_plain.append(timed_one(plain))
+            launches += c1 - c0                        # over the K timed headline steps
+            launches_plain += P.kernel_launches() - c1
     ms_mixed, ms_plain = float(np.mean(t_mixed)), float(np.mean(t_plain))
     if ws > 1:
         t = torch.tensor([ms_mixed, ms_plain], device=dev)
@@ -240,41 +242,66 @@ def main():
 
     # accuracy of this very run (factors of the timed input against its known spectrum)
     info_m = P.info_dict(mixed[5])[0]
-    sig = mixed[2][0].double().cpu().numpy()
-    sig_err = float(np.max(np.abs(sig - s0)) / s0[0])
 
-    # roofline of the product kernel: CUDA events around each launch on its stream
+    def accuracy(bufs):
+        _, U, S, VT, *_ = bufs
+        u, sg, vt, a = U[0].double(), S[0].double(), VT[0].double(), A[0].double()
+        eye = torch.eye(N, dtype=torch.float64, device=dev)
+        return {"sigma_err_rel_smax": float((sg.cpu() - torch.from_numpy(s0)).abs().max() / s0[0]),
+                "recon": float(torch.linalg.matrix_norm(a - (u * sg) @ vt) / torch.linalg.matrix_norm(a)),
+                "ortho_u": float(torch.linalg.matrix_norm(u.T @ u - eye) / N ** 0.5),
+                "ortho_v": float(torch.linalg.matrix_norm(vt @ vt.T - eye) / N ** 0.5)}
+
+    acc_m, acc_p = accuracy(mixed), accuracy(plain)
+    sig_err = acc_m["sigma_err_rel_smax"]
+
+    # roofline: CUDA events around each launch of the tridiagonalization (the dominant
+    # kernel) and of the tcgen05 product kernel, on their stream, in one extra step of each path
     peaks, peak_src = _peaks()
+    NCLS = 5                                   # PSVD_PROF_CLASSES
     L.psvd_profile_enable(1)
     step(mixed, A)
     torch.cuda.synchronize()
-    prof = (ctypes.c_double * 16)()
-    L.psvd_profile_read(prof)
+    prof_m = (ctypes.c_double * (4 * NCLS))()
+    L.psvd_profile_read(prof_m)
     step(plain, A)
     torch.cuda.synchronize()
-    prof_p = (ctypes.c_double * 16)()
+    prof_p = (ctypes.c_double * (4 * NCLS))()
     L.psvd_profile_read(prof_p)
     L.psvd_profile_enable(0)
+
+    def cls(arr, c):
+        return {"launches": int(arr[4 * c]), "ms": arr[4 * c + 1], "work": arr[4 * c + 2], "max_ms": arr[4 * c + 3]}
+
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     bf16_peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
     tf32_peak = bf16_peak * (1.1 / 2.25)
-    # per class: (launches, ms, flops, max ms); split-TF32 issues 3 TF32 products per flop
-    cls_peak = [bf16_peak, tf32_peak, tf32_peak / 3.0, None]
-    per = {}
-    for c, name in enumerate(["bf16", "tf32", "tf32x3", "mixed"]):
-        nl, ms, fl = prof[4 * c], prof[4 * c + 1], prof[4 * c + 2]
-        if nl > 0:
-            per[name] = {"launches": int(nl), "ms": ms, "tflops": fl / (ms * 1e-3) / 1e12}
-    # the per-matrix-precision launches (polar steps) dominate the mixed path
-    pm = prof[12:16]
-    pp = prof_p[8:12]     # plain path: split-TF32 class
-    ach_m = pm[2] / (pm[1] * 1e-3) / 1e12 if pm[1] > 0 else 0.0
-    ach_p = pp[2] / (pp[1] * 1e-3) / 1e12 if pp[1] > 0 else 0.0
-    roofline = {"bound": "tensor", "achieved": ach_p, "peak": tf32_peak / 3.0, "unit": "TFLOP/s",
-                "frac": ach_p / (tf32_peak / 3.0), "traffic": None,
-                "kernel": "gemm_tn_kernel (tcgen05 split-TF32, plain path, all launches of one step)",
-                "peak_src": f"{peak_src} bf16 sustained {bf16_peak:.0f} x 1.1/2.25 (TF32) / 3 (split-TF32)",
-                "mixed_path_kernel_tflops": ach_m, "mixed_path_classes": per,
-                "gemm_ms_share_plain": pp[1] / ms_plain if ms_plain else None}
+    trd = cls(prof_m, 4)
+    trd_gbs = trd["work"] / (trd["ms"] * 1e-3) / 1e9 if trd["ms"] > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": trd_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": trd_gbs / hbm_peak,
+                "traffic": None,
+                "kernel": "sytrd_kernel (Householder tridiagonalization of H, eigensolver stage 1; one launch)",
+                "algorithmic_bytes": trd["work"], "ms": trd["ms"], "share_of_step": trd["ms"] / ms_mixed,
+                "peak_src": f"{peak_src} HBM copy {hbm_peak:.0f} GB/s",
+                "note": "read+write of the trailing matrix every step, 8 sum (n-k-2)^2 bytes; the 64 MB "
+                        "working matrix is served from L2, so the fraction can exceed what HBM alone allows"}
+    # polar GEMM chain (per-matrix precision launches of the mixed path) against the
+    # precision-weighted peak of the steps it ran
+    mix = cls(prof_m, 3)
+    st = [info_m["steps_bf16"], info_m["steps_tf32"], info_m["steps_3xtf32"]]
+    pk = [bf16_peak, tf32_peak, tf32_peak / 3.0]
+    wpeak = sum(st) / sum(k / p for k, p in zip(st, pk)) if sum(st) else bf16_peak
+    chain_tf = mix["work"] / (mix["ms"] * 1e-3) / 1e12 if mix["ms"] > 0 else 0.0
+    x3 = cls(prof_p, 2)
+    plain_tf = x3["work"] / (x3["ms"] * 1e-3) / 1e12 if x3["ms"] > 0 else 0.0
+    tensor = {"polar_chain_mixed": {"achieved": chain_tf, "peak": wpeak, "unit": "TFLOP/s", "frac": chain_tf / wpeak,
+                                    "launches": mix["launches"], "ms": mix["ms"],
+                                    "peak_src": f"{peak_src} bf16 sustained {bf16_peak:.0f}, TF32 x1.1/2.25, "
+                                                f"split-TF32 /3, weighted by steps {st}"},
+              "split_tf32_all_plain": {"achieved": plain_tf, "peak": tf32_peak / 3.0, "unit": "TFLOP/s",
+                                       "frac": plain_tf / (tf32_peak / 3.0), "launches": x3["launches"],
+                                       "ms": x3["ms"]},
+              "product_kernel_ms_share_mixed": sum(cls(prof_m, c)["ms"] for c in range(4)) / ms_mixed}
 
     # end to end through the C ABI with host buffers: H2D of A, D2H of dA and sigma
     A_host = A.cpu().pin_memory()
@@ -301,13 +328,18 @@ def main():
                                        f"s_i = {KAPPA:g}^((n-i)/(n-1)), eps=1e-8, kreg Algorithm 4",
                            "path": "mixed: BF16->TF32->split-TF32 polish + eigenbasis correction, CANS delta=0.99",
                            "plain_ms": ms_plain, "speedup_mixed_vs_plain": ms_plain / ms_mixed,
+                           "median_ms": {"mixed": float(np.median(t_mixed)), "plain": float(np.median(t_plain))},
+                           "accuracy_plain": acc_p,
                            "l2": "512 MB buffer written between timed steps",
                            "launches_per_step": {"mixed": launches // max(1, args.steps),
                                                  "plain": launches_plain // max(1, args.steps)},
-                           "accuracy_mixed": {"sigma_err_rel_smax": sig_err, "ortho_resid": info_m["ortho_resid"],
+                           "accuracy_mixed": {**acc_m, "polar_ortho_resid": info_m["ortho_resid"],
+                                              "corr_max": info_m["corr_max"],
+                                              "prec_fallback": info_m["prec_fallback"],
                                               "polar_steps": [info_m["steps_bf16"], info_m["steps_tf32"],
                                                               info_m["steps_3xtf32"]]}},
                 "roofline": roofline,
+                "tensor": tensor,
                 "clocks": clk.summary(),
                 "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": N * N * 4,
                         "d2h_bytes_per_step": N * N * 4 + N * 4},

@@ -46,9 +46,13 @@ extern "C" {
 #define PSVD_ERR_UNSUPPORTED   -6   /* device is not sm_103 / sm_100 class            */
 
 /* ---- options ----------------------------------------------------------- */
-#define PSVD_PREC_FP32    0   /* every product FP32-accurate (split hi+lo TF32, "3xTF32") */
-#define PSVD_PREC_MIXED   1   /* BF16 early steps -> TF32 -> 3xTF32 polish, chosen from
-                                 the measured orthogonality residual                       */
+#define PSVD_PREC_FP32       0   /* every product FP32-accurate (split hi+lo TF32, "3xTF32") */
+#define PSVD_PREC_MIXED      1   /* TF32 steps -> 3xTF32 polish, switched per matrix from the
+                                    measured orthogonality residual                          */
+#define PSVD_PREC_MIXED_BF16 2   /* BF16 early steps -> TF32 -> 3xTF32 polish; the BF16
+                                    rounding leaves a rotation that the eigenbasis correction
+                                    undoes only to first order (reconstruction ~1e-5 at
+                                    n = 4096, kappa = 10)                                    */
 
 #define PSVD_SCHED_CANS     0 /* conservative CANS: preprocessing for [t,1] then greedy
                                  optimal cubics from [1-delta, 1+delta] (Appendix B.8)     */
@@ -79,12 +83,30 @@ typedef struct psvd_info {
     int   qr_fallback;     /* 1 if U was re-orthogonalized by QR (Algorithm 1 step 8)    */
     int   sched_fallback;  /* 1 if the learned schedule missed tol and the conservative
                               schedule was rerun                                          */
+    int   prec_fallback;   /* svd_fwd, mixed precision: 1 if the eigenbasis correction
+                              was too large to trust (corr_max above PSVD_MIXED_CORR_MAX)
+                              and the matrix was recomputed on the FP32-accurate path    */
     int   steps_bf16;      /* steps taken in each precision (mixed path)                 */
     int   steps_tf32;
     int   steps_3xtf32;
     float ortho_resid;     /* final ||W^T W - I||_F / sqrt(n)                            */
     float scale;           /* sqrt(||M||_1 ||M||_inf) of Algorithm 2                     */
+    float corr_max;        /* svd_fwd, mixed precision: max |X_ij| of the rotation that
+                              the eigenbasis correction applied (0 otherwise)           */
+    float range_resid;     /* svd_fwd, mixed precision, m > n: ||A - W W^T A||_F / ||A||_F,
+                              the part of A outside the computed polar factor's column
+                              space (0 otherwise)                                        */
 } psvd_info;
+
+/* Mixed-precision svd_fwd keeps a matrix's BF16/TF32 result only while both checks
+ * hold, and recomputes it on the FP32-accurate path otherwise (prec_fallback = 1):
+ *  - corr_max <= PSVD_MIXED_CORR_MAX: the eigenbasis correction is first order, its
+ *    error grows like corr_max^2;
+ *  - range_resid <= PSVD_MIXED_RANGE_MAX: the polynomial steps multiply X on the right
+ *    and never repair its column space, so for m > n the rounding of the low-precision
+ *    steps leaves part of A outside it, and that part is missing from U S V^T. */
+#define PSVD_MIXED_CORR_MAX 2e-3
+#define PSVD_MIXED_RANGE_MAX 5e-6
 
 /* ---- workspace queries ---------------------------------------------------- */
 size_t psvd_polar_workspace_bytes(int64_t batch, int64_t m, int64_t n, const psvd_opts *opts);
@@ -202,13 +224,21 @@ const char *psvd_last_error(void);
 uint64_t psvd_kernel_launch_count(void);
 
 /* Measurement hooks (no counterpart in the paper; used by the benchmark's roofline).
- * psvd_profile_enable(1) makes every launch of the tcgen05 product kernel record a pair of
- * CUDA events on its stream (up to 8192 launches; the call creates the events once), 0
- * turns it off.  psvd_profile_read fills 16 doubles: for precision class c = 0 BF16,
- * 1 TF32, 2 split-TF32, 3 per-matrix (mixed) -- out[4c] launches, out[4c+1] summed
- * kernel milliseconds, out[4c+2] summed algorithmic flops (2MNK, M(M+1)K for the
- * symmetric Gram), out[4c+3] longest launch in ms -- then clears the record.  Host
+ * psvd_profile_enable(1) makes every launch of the tcgen05 product kernel and of the
+ * tridiagonalization record a pair of CUDA events on its stream (up to 8192 launches;
+ * the call creates the events once), 0 turns it off.  psvd_profile_read fills
+ * 4 * PSVD_PROF_CLASSES doubles: for class c -- out[4c] launches, out[4c+1] summed
+ * kernel milliseconds, out[4c+2] summed algorithmic work, out[4c+3] longest launch in ms
+ * -- then clears the record.  Work is flops for the product kernel (2MNK; M(M+1)K for
+ * the symmetric Gram) and bytes for the tridiagonalization (its step k reads and
+ * writes the (n-k-2)^2 trailing entries: sum over k of 8 (n-k-2)^2 per matrix).  Host
  * pointer; synchronizes on the recorded events. */
+#define PSVD_PROF_BF16     0   /* product kernel, BF16 operands        */
+#define PSVD_PROF_TF32     1   /* product kernel, TF32 operands        */
+#define PSVD_PROF_TF32X3   2   /* product kernel, split-TF32 operands  */
+#define PSVD_PROF_MIXED    3   /* product kernel, per-matrix precision */
+#define PSVD_PROF_TRD      4   /* tridiagonalization (eigh stage 1)    */
+#define PSVD_PROF_CLASSES  5
 int psvd_profile_enable(int on);
 int psvd_profile_read(double *out);
 

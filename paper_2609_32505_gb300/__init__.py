@@ -18,7 +18,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_PKG, "libpsvd.so")
 _lib = None
 
-PREC_FP32, PREC_MIXED = 0, 1
+PREC_FP32, PREC_MIXED, PREC_MIXED_BF16 = 0, 1, 2
 SCHED_CANS, SCHED_LEARNED, SCHED_NS = 0, 1, 2
 GEMM_BF16, GEMM_TF32, GEMM_TF32X3 = 0, 1, 2
 
@@ -38,9 +38,12 @@ class Opts(ctypes.Structure):
                 ("eps_qr", ctypes.c_double), ("lower_bound", ctypes.c_void_p), ("budget", ctypes.c_int)]
 
 
-INFO_FIELDS = ["status", "iters", "qr_fallback", "sched_fallback", "steps_bf16", "steps_tf32",
-               "steps_3xtf32", "ortho_resid", "scale"]
-INFO_INTS = 7   # the first 7 fields are int32, the last 2 float32
+INFO_FIELDS = ["status", "iters", "qr_fallback", "sched_fallback", "prec_fallback", "steps_bf16", "steps_tf32",
+               "steps_3xtf32", "ortho_resid", "scale", "corr_max", "range_resid"]
+INFO_INTS = 8   # the first 8 fields are int32, the rest float32
+INFO_WORDS = len(INFO_FIELDS)
+MIXED_CORR_MAX = 2e-3    # PSVD_MIXED_CORR_MAX of psvd.h
+MIXED_RANGE_MAX = 5e-6   # PSVD_MIXED_RANGE_MAX of psvd.h
 
 
 def build(force: bool = False) -> str:
@@ -143,7 +146,7 @@ def make_opts(precision: int = PREC_FP32, schedule: int = SCHED_CANS, delta: flo
 
 
 def info_dict(info: torch.Tensor):
-    """Decodes a (batch, 9) int32 device info array into a list of dicts."""
+    """Decodes a (batch, INFO_WORDS) int32 device info array into a list of dicts."""
     raw = info.cpu()
     ints = raw[:, :INFO_INTS].tolist()
     flts = raw[:, INFO_INTS:].contiguous().view(torch.float32).tolist()
@@ -163,7 +166,7 @@ def polar(a: torch.Tensor, opts: Opts | None = None, want_h: bool = True, return
     o = opts or make_opts()
     W = torch.empty_like(A)
     H = torch.empty(bt, n, n, device=A.device, dtype=torch.float32) if want_h else None
-    info = torch.zeros(bt, 9, device=A.device, dtype=torch.int32)
+    info = torch.zeros(bt, INFO_WORDS, device=A.device, dtype=torch.int32)
     L = lib()
     ws = _workspace(L.psvd_polar_workspace_bytes(bt, m, n, ctypes.byref(o)), A.device)
     _check(L.psvd_polar_fwd(_ptr(A), _ptr(W), _ptr(H), bt, m, n, ctypes.byref(o), _ptr(ws), ws.numel(),
@@ -192,7 +195,7 @@ def svd_fwd(a: torch.Tensor, opts: Opts | None = None, return_info: bool = False
     U = torch.empty_like(A)
     S = torch.empty(bt, n, device=A.device, dtype=torch.float32)
     VT = torch.empty(bt, n, n, device=A.device, dtype=torch.float32)
-    info = torch.zeros(bt, 9, device=A.device, dtype=torch.int32)
+    info = torch.zeros(bt, INFO_WORDS, device=A.device, dtype=torch.int32)
     L = lib()
     ws = _workspace(L.psvd_svd_workspace_bytes(bt, m, n, ctypes.byref(o)), A.device)
     _check(L.psvd_svd_fwd(_ptr(A), _ptr(U), _ptr(S), _ptr(VT), bt, m, n, ctypes.byref(o), _ptr(ws), ws.numel(),

@@ -809,9 +809,15 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
         PSVD_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sytrd_kernel, kTrdThreads, smem));
         if (occ * num_sms() < w.groups * P.g) return cuda_fail(cudaErrorCooperativeLaunchTooLarge, __FILE__, __LINE__);
         void *args[] = {&P};
+        const bool prof = prof_on();
+        if (prof) prof_begin(st);
         PSVD_TRY(cudaLaunchCooperativeKernel((void *)sytrd_kernel, dim3(w.groups * P.g), dim3(kTrdThreads), args,
                                              smem, st));
         count_launch(1);
+        if (prof) {
+            const double j = (double)std::max(0, n - 2);   // sum_{t=1}^{n-2} 8 t^2
+            prof_end(st, 8.0 * j * (j + 1) * (2 * j + 1) / 6.0 * B, PSVD_PROF_TRD);
+        }
     }
     // 2. eigenvalues
     double *tn = reinterpret_cast<double *>(w.S2hi);   // B doubles of scratch (S2 is free until stage 4)

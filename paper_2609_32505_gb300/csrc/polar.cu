@@ -204,6 +204,8 @@ struct EpiApply {
 };
 
 // Per-matrix decision after the Gram of step k.
+// mixed: 0 every step split-TF32; 1 TF32 until the residual drops below kTauTF32; 2 BF16
+// above kTauBF16 first.  The precision never decreases from one step to the next.
 __global__ void decide_kernel(int k, int B, int n, double tol, int mixed, int learned, int kcap, int *done,
                               int *fin, int *status, int *prec, int *steps, const double *res, float *fres,
                               const int *budget, int *fallback, int *notdone) {
@@ -223,7 +225,7 @@ __global__ void decide_kernel(int k, int B, int n, double tol, int mixed, int le
     }
     int pn = PREC_TF32X3;
     if (mixed) {
-        const int want = r > kTauBF16 ? PREC_BF16 : (r > kTauTF32 ? PREC_TF32 : PREC_TF32X3);
+        const int want = (mixed == 2 && r > kTauBF16) ? PREC_BF16 : (r > kTauTF32 ? PREC_TF32 : PREC_TF32X3);
         pn = want > pk ? want : pk;
     }
     prec[(long long)(k + 1) * B + b] = pn;
@@ -293,6 +295,9 @@ __global__ void polar_info_kernel(int B, const int *status, const int *fin, cons
     r.iters = steps[b] + steps[B + b] + steps[2 * B + b];
     r.qr_fallback = 0;
     r.sched_fallback = fallback[b];
+    r.prec_fallback = 0;
+    r.corr_max = 0.f;
+    r.range_resid = 0.f;
     r.steps_bf16 = steps[b];
     r.steps_tf32 = steps[B + b];
     r.steps_3xtf32 = steps[2 * B + b];
@@ -307,7 +312,7 @@ static int launch_step(PolarWS &w, int k, bool apply, double tol, bool learned, 
     const int par = k & 1, npar = (k + 1) & 1;
     // Gram: A = B = X^T (n x m, K = m), upper-triangle tiles
     {
-        MatView v16 = w.mixed ? view_of16(w.XT16[par], n, m, w.ldm, (long long)n * w.ldm, B) : MatView();
+        MatView v16 = w.bf16 ? view_of16(w.XT16[par], n, m, w.ldm, (long long)n * w.ldm, B) : MatView();
         MatView vhi = view_of(w.XThi[par], n, m, w.ldm, (long long)n * w.ldm, B);
         MatView vlo = view_of(w.XTlo[par], n, m, w.ldm, (long long)n * w.ldm, B);
         GemmShape s;
@@ -322,11 +327,12 @@ static int launch_step(PolarWS &w, int k, bool apply, double tol, bool learned, 
         e.prec = w.prec + (long long)k * B;
         e.res = w.res + (long long)k * B;
         e.P16 = w.P16; e.Phi = w.Phi; e.Plo = w.Plo; e.ldp = w.ldn;
-        cudaError_t er = launch_gemm(w.mixed ? &v16 : nullptr, w.mixed ? &v16 : nullptr, &vhi, &vlo, &vhi, &vlo, s,
+        cudaError_t er = launch_gemm(w.bf16 ? &v16 : nullptr, w.bf16 ? &v16 : nullptr, &vhi, &vlo, &vhi, &vlo, s,
                                      B, e, st);
         if (er != cudaSuccess) return PSVD_ERR_CUDA;
     }
-    decide_kernel<<<(B + 127) / 128, 128, 0, st>>>(k, B, n, tol, w.mixed ? 1 : 0, learned ? 1 : 0, w.kcap, w.done,
+    const int ladder = w.bf16 ? 2 : (w.mixed ? 1 : 0);
+    decide_kernel<<<(B + 127) / 128, 128, 0, st>>>(k, B, n, tol, ladder, learned ? 1 : 0, w.kcap, w.done,
                                                     w.fin, w.status, w.prec, w.steps, w.res, fres, w.budget,
                                                     w.fallback, w.notdone);
     count_launch(1);
@@ -334,10 +340,10 @@ static int launch_step(PolarWS &w, int k, bool apply, double tol, bool learned, 
     if (!apply) return PSVD_OK;
     // Apply: A = X (m x n, K = n), B = P (n x n, symmetric)
     {
-        MatView a16 = w.mixed ? view_of16(w.X16[par], m, n, w.ldn, (long long)m * w.ldn, B) : MatView();
+        MatView a16 = w.bf16 ? view_of16(w.X16[par], m, n, w.ldn, (long long)m * w.ldn, B) : MatView();
         MatView ahi = view_of(w.Xhi[par], m, n, w.ldn, (long long)m * w.ldn, B);
         MatView alo = view_of(w.Xlo[par], m, n, w.ldn, (long long)m * w.ldn, B);
-        MatView b16 = w.mixed ? view_of16(w.P16, n, n, w.ldn, (long long)n * w.ldn, B) : MatView();
+        MatView b16 = w.bf16 ? view_of16(w.P16, n, n, w.ldn, (long long)n * w.ldn, B) : MatView();
         MatView bhi = view_of(w.Phi, n, n, w.ldn, (long long)n * w.ldn, B);
         MatView blo = view_of(w.Plo, n, n, w.ldn, (long long)n * w.ldn, B);
         GemmShape s;
@@ -352,7 +358,7 @@ static int launch_step(PolarWS &w, int k, bool apply, double tol, bool learned, 
         e.X16 = w.X16[npar]; e.XT16 = w.XT16[npar];
         e.Xhi = w.Xhi[npar]; e.Xlo = w.Xlo[npar]; e.XThi = w.XThi[npar]; e.XTlo = w.XTlo[npar];
         e.ldn = w.ldn; e.ldm = w.ldm;
-        cudaError_t er = launch_gemm(w.mixed ? &a16 : nullptr, w.mixed ? &b16 : nullptr, &ahi, &alo, &bhi, &blo, s,
+        cudaError_t er = launch_gemm(w.bf16 ? &a16 : nullptr, w.bf16 ? &b16 : nullptr, &ahi, &alo, &bhi, &blo, s,
                                      B, e, st);
         if (er != cudaSuccess) return PSVD_ERR_CUDA;
     }
@@ -410,7 +416,7 @@ static int prepare_x0(const float *A, PolarWS &w, cudaStream_t st, const int *sk
     SplitOut r, t;
     r.ld = w.ldn; r.bstride = (long long)m * w.ldn;
     t.ld = w.ldm; t.bstride = (long long)n * w.ldm;
-    if (w.mixed) { r.h16 = w.X16[0]; t.h16 = w.XT16[0]; }
+    if (w.bf16) { r.h16 = w.X16[0]; t.h16 = w.XT16[0]; }
     else { r.hi = w.Xhi[0]; r.lo = w.Xlo[0]; t.hi = w.XThi[0]; t.lo = w.XTlo[0]; }
     if (prepare_operand(A, n, (long long)m * n, B, m, n, false, 1.f, w.scale, r, st, skip) ||
         prepare_operand(A, n, (long long)m * n, B, m, n, true, 1.f, w.scale, t, st, skip))
@@ -431,7 +437,7 @@ int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &
         cudaMemsetAsync(w.misc, 0, sizeof(int) * 8, st) ||
         cudaMemsetAsync(w.err, 0, sizeof(unsigned) * 4, st))
         return PSVD_ERR_CUDA;
-    const int prec0 = w.mixed ? PREC_BF16 : PREC_TF32X3;
+    const int prec0 = w.bf16 ? PREC_BF16 : (w.mixed ? PREC_TF32 : PREC_TF32X3);
     polar_init_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, prec0, w.done, w.fin, w.status, w.prec, w.steps,
                                                         w.fallback);
     if (l1_norms(A, B, m, n, w.rowsum, w.colsum, w.nonfinite, st) != cudaSuccess) return PSVD_ERR_CUDA;
@@ -514,7 +520,7 @@ int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &
 using namespace psvd;
 
 static bool opts_ok(const psvd_opts &o) {
-    return (o.precision == PSVD_PREC_FP32 || o.precision == PSVD_PREC_MIXED) &&
+    return (o.precision == PSVD_PREC_FP32 || o.precision == PSVD_PREC_MIXED || o.precision == PSVD_PREC_MIXED_BF16) &&
            (o.schedule >= PSVD_SCHED_CANS && o.schedule <= PSVD_SCHED_NS) && o.delta > 0 && o.delta < 1 &&
            o.pre_iters >= 0 && o.pre_iters <= 8 && o.max_iter >= 1 && o.max_iter <= 64 && o.tol > 0 &&
            o.eps_qr > 0 && (o.schedule != PSVD_SCHED_LEARNED || o.lower_bound != nullptr);
@@ -532,7 +538,7 @@ extern "C" size_t psvd_polar_workspace_bytes(int64_t batch, int64_t m, int64_t n
     if (batch <= 0 || m <= 0 || n <= 0) return 0;
     Sizer s;
     PolarWS w;
-    w.carve(s, (int)batch, (int)m, (int)n, polar_kcap(o), o.precision == PSVD_PREC_MIXED);
+    w.carve(s, (int)batch, (int)m, (int)n, polar_kcap(o), o.precision);
     return s.used + 256;
 }
 
@@ -546,7 +552,7 @@ extern "C" int psvd_polar_fwd(const float *A, float *W, float *H, int64_t batch,
     if (ws_bytes < psvd_polar_workspace_bytes(batch, m, n, &o)) return PSVD_ERR_WORKSPACE;
     Carver cv(ws, ws_bytes);
     PolarWS w;
-    w.carve(cv, (int)batch, (int)m, (int)n, polar_kcap(o), o.precision == PSVD_PREC_MIXED);
+    w.carve(cv, (int)batch, (int)m, (int)n, polar_kcap(o), o.precision);
     if (cv.overflow) return PSVD_ERR_WORKSPACE;
     return polar_forward(A, W, H, H != nullptr, w, o, info, static_cast<cudaStream_t>(stream));
 }
@@ -596,7 +602,7 @@ extern "C" int psvd_polar_fwd_noalloc(const float *A, float *W, float *H, int64_
     }
     Carver cv(scratch, kNoAllocScratchBytes);
     PolarWS w;
-    w.carve(cv, (int)batch, (int)m, (int)n, polar_kcap(o), o.precision == PSVD_PREC_MIXED);
+    w.carve(cv, (int)batch, (int)m, (int)n, polar_kcap(o), o.precision);
     if (cv.overflow) return PSVD_ERR_WORKSPACE;
     return polar_forward(A, W, H, H != nullptr, w, o, info, static_cast<cudaStream_t>(stream));
 }

@@ -5,12 +5,19 @@
 
 namespace psvd {
 
-constexpr double kTauBF16 = 5e-2;   // mixed path: leave BF16 once the residual is below this
-constexpr double kTauTF32 = 2e-3;   // ... and TF32 once below this (3xTF32 polish afterwards)
+#ifndef PSVD_TAU_BF16
+#define PSVD_TAU_BF16 5e-2
+#endif
+#ifndef PSVD_TAU_TF32
+#define PSVD_TAU_TF32 2e-3
+#endif
+constexpr double kTauBF16 = PSVD_TAU_BF16;   // mixed path: leave BF16 once the residual is below this
+constexpr double kTauTF32 = PSVD_TAU_TF32;   // ... and TF32 once below this (3xTF32 polish afterwards)
 
 struct PolarWS {
     int B = 0, m = 0, n = 0, kcap = 0;
-    bool mixed = false;
+    bool mixed = false;     // precision switched per matrix and step (PSVD_PREC_MIXED*)
+    bool bf16 = false;      // BF16 early steps and their operand copies (PSVD_PREC_MIXED_BF16)
     long long ldn = 0, ldm = 0;
     // iterate buffers, double-buffered by step parity
     __nv_bfloat16 *X16[2] = {}, *XT16[2] = {};
@@ -30,12 +37,14 @@ struct PolarWS {
     unsigned *err = nullptr;
 
     template <class C>
-    void carve(C &cv, int B_, int m_, int n_, int kcap_, bool mixed_) {
-        B = B_; m = m_; n = n_; kcap = kcap_; mixed = mixed_;
+    void carve(C &cv, int B_, int m_, int n_, int kcap_, int precision) {
+        B = B_; m = m_; n = n_; kcap = kcap_;
+        mixed = precision != PSVD_PREC_FP32;
+        bf16 = precision == PSVD_PREC_MIXED_BF16;
         ldn = pad_ld(n); ldm = pad_ld(m);
         const long long B64 = B;
         for (int p = 0; p < 2; ++p) {
-            if (mixed) {
+            if (bf16) {
                 X16[p] = cv.template take<__nv_bfloat16>(B64 * m * ldn);
                 XT16[p] = cv.template take<__nv_bfloat16>(B64 * n * ldm);
             }
@@ -44,7 +53,7 @@ struct PolarWS {
             XThi[p] = cv.template take<float>(B64 * n * ldm);
             XTlo[p] = cv.template take<float>(B64 * n * ldm);
         }
-        if (mixed) P16 = cv.template take<__nv_bfloat16>(B64 * n * ldn);
+        if (bf16) P16 = cv.template take<__nv_bfloat16>(B64 * n * ldn);
         Phi = cv.template take<float>(B64 * n * ldn);
         Plo = cv.template take<float>(B64 * n * ldn);
         AThi = cv.template take<float>(B64 * n * ldm);

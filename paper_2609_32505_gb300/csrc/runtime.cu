@@ -136,17 +136,18 @@ int psvd_profile_enable(int on) {
     return PSVD_OK;
 }
 
-// out[4 * c + {0,1,2,3}] for class c = 0 (BF16), 1 (TF32), 2 (split TF32), 3 (per-matrix
-// precision): launches, total ms, total algorithmic flops, max single-launch ms.
+// out[4 * c + {0,1,2,3}] for class c (PSVD_PROF_*): launches, total ms, total algorithmic
+// work (flops for the product kernel, bytes for the tridiagonalization), max single-launch ms.
 int psvd_profile_read(double *out) {
     using namespace psvd;
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    for (int i = 0; i < 16; ++i) out[i] = 0.0;
+    for (int i = 0; i < 4 * PSVD_PROF_CLASSES; ++i) out[i] = 0.0;
     for (int i = 0; i < g_prof.n; ++i) {
         if (cudaEventSynchronize(g_prof.ev[2 * i + 1]) != cudaSuccess) return PSVD_ERR_CUDA;
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]) != cudaSuccess) return PSVD_ERR_CUDA;
-        const int c = g_prof.prec[i] < 0 ? 3 : g_prof.prec[i];
+        const int c = g_prof.prec[i] < 0 ? PSVD_PROF_MIXED : g_prof.prec[i];
+        if (c >= PSVD_PROF_CLASSES) continue;
         out[4 * c] += 1.0;
         out[4 * c + 1] += ms;
         out[4 * c + 2] += g_prof.flops[i];

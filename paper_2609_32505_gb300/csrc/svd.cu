@@ -12,6 +12,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <vector>
+
 #include "eigh.cuh"
 #include "polar.cuh"
 
@@ -159,19 +161,87 @@ __global__ void skewT_kernel(const float *Hraw, int n, float *hi, float *lo, lon
     lo[(long long)b * n * ld + (long long)i * ld + j] = ll;
 }
 
-// X = Ktilde / (s_i + s_j) (skew); writes X (tf32) and -X (for B operands), and
-// the two update factors F = X + X^2/2 and Ft = -X + X^2/2 once X^2 is known.
-__global__ void corr_x_kernel(const float *Kt, const float *S, int n, float *X, float *Xneg, long long ld) {
+// X = Ktilde / (s_i + s_j) (skew); writes X split into TF32 hi/lo (the first-order
+// product X V^T is taken in split-TF32) and -X_hi (B operand of X^2).
+// Also records max |X_ij| per matrix in xmax (float bits; the values are >= 0, and a NaN
+// compares above every finite value, so it forces the fallback).
+__global__ void corr_x_kernel(const float *Kt, const float *S, int n, float *X, float *Xlo, float *Xneg, long long ld,
+                              unsigned *xmax) {
     const int b = blockIdx.z;
     const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
-    if (i >= n || j >= n) return;
-    const float si = S[(long long)b * n + i], sj = S[(long long)b * n + j];
-    const float den = si + sj;
-    float k = Kt[(long long)b * n * n + (long long)i * n + j];
-    k = 0.5f * (k - Kt[(long long)b * n * n + (long long)j * n + i]);   // exact skew part
-    const float x = den > 0.f ? k / den : 0.f;
-    X[(long long)b * n * ld + (long long)i * ld + j] = tf32_round(x);
-    Xneg[(long long)b * n * ld + (long long)i * ld + j] = tf32_round(-x);
+    float ax = 0.f;
+    if (i < n && j < n) {
+        const float si = S[(long long)b * n + i], sj = S[(long long)b * n + j];
+        const float den = si + sj;
+        float k = Kt[(long long)b * n * n + (long long)i * n + j];
+        k = 0.5f * (k - Kt[(long long)b * n * n + (long long)j * n + i]);   // exact skew part
+        const float x = den > 0.f ? k / den : 0.f;
+        float xh, xl;
+        split_tf32(x, xh, xl);
+        X[(long long)b * n * ld + (long long)i * ld + j] = xh;
+        Xlo[(long long)b * n * ld + (long long)i * ld + j] = xl;
+        Xneg[(long long)b * n * ld + (long long)i * ld + j] = -xh;
+        ax = fabsf(x);
+    }
+    unsigned bits = __float_as_uint(ax);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, o));
+    if (((threadIdx.y * 16 + threadIdx.x) & 31) == 0 && bits) atomicMax(&xmax[b], bits);
+}
+
+// ||A||_F^2 and ||A - W Hhat||_F^2 per matrix (Hhat = W^T A): the part of A outside the
+// column space of W.  Nothing is stored.
+struct EpiRange {
+    int m, n;
+    const float *A;
+    double *sums;     // [B][2]
+    struct Acc { double a, r; };
+    PSVD_DEV void begin(Acc &s) const { s.a = 0.0; s.r = 0.0; }
+    PSVD_DEV void chunk(Acc &s, int b, int r, int c0, int, int, float (&v)[16]) const {
+        if (r >= m) return;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int c = c0 + i;
+            if (c >= n) break;
+            const float a = A[(long long)b * m * n + (long long)r * n + c];
+            const float d = a - v[i];
+            s.a += (double)a * a;
+            s.r += (double)d * d;
+        }
+    }
+    PSVD_DEV void finish(Acc &s, int b, int, int) const {
+        const double a = warp_sum(s.a), r = warp_sum(s.r);
+        if ((threadIdx.x & 31) == 0) {
+            if (a != 0.0) atomicAdd(&sums[2 * b], a);
+            if (r != 0.0) atomicAdd(&sums[2 * b + 1], r);
+        }
+    }
+};
+
+// Matrices whose correction rotation or range residual is too large to trust are
+// flagged for the FP32-accurate rerun; records both in info.
+__global__ void mixed_flag_kernel(const unsigned *xmax, const double *rsums, int B, float corr_limit,
+                                  float range_limit, int *mflag, int *count, psvd_info *info) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const float x = __uint_as_float(xmax[b]);
+    float rr = 0.f;
+    if (rsums) rr = rsums[2 * b] > 0.0 ? (float)sqrt(rsums[2 * b + 1] / rsums[2 * b]) : 0.f;
+    const int f = !(x <= corr_limit) || !(rr <= range_limit);
+    mflag[b] = f;
+    if (f) atomicAdd(count, 1);
+    if (info) { info[b].corr_max = x; info[b].range_resid = rr; }
+}
+
+// Results of the FP32-accurate rerun replace the flagged matrices' records.
+__global__ void info_scatter_kernel(psvd_info *info, const psvd_info *infoc, const int *idx, int F) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= F) return;
+    psvd_info r = infoc[j];
+    r.prec_fallback = 1;
+    r.corr_max = info[idx[j]].corr_max;
+    r.range_resid = info[idx[j]].range_resid;
+    info[idx[j]] = r;
 }
 
 // Second-order singular values of Sigma + K: diag(e^-X (Sigma + K) e^-X)_i =
@@ -192,19 +262,15 @@ __global__ void sigma_refresh_kernel(const float *X, const float *S, int n, long
     }
 }
 
-// F = X + X^2/2 - X^4/8 and Ft = -X + X^2/2 - X^4/8: (I + F)(I + F)^T = I + O(X^8), the
-// -X^4/8 term being one Newton-Schulz step on I + X + X^2/2 (whose Gram is I + X^4/4).
-__global__ void corr_f_kernel(const float *X2, const float *X4, const float *X, int n, long long ld, float *F,
-                              float *Ft) {
+// Second-order part of the update, h = X^2/2 - X^4/8 (TF32 operand): with it,
+// I + X + h and I - X + h satisfy (I + F)(I + F)^T = I + O(X^8), the -X^4/8 term being
+// one Newton-Schulz step on I + X + X^2/2 (whose Gram is I + X^4/4).
+__global__ void corr_h_kernel(const float *X2, const float *X4, int n, long long ld, float *Hh) {
     const int b = blockIdx.z;
     const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
     if (i >= n || j >= n) return;
-    const long long o = (long long)b * n * ld + (long long)i * ld + j;
     const long long p = (long long)b * n * n + (long long)i * n + j;
-    const float x = X[o];
-    const float h = 0.5f * X2[p] - 0.125f * X4[p];
-    F[o] = tf32_round(x + h);
-    Ft[o] = tf32_round(-x + h);
+    Hh[(long long)b * n * ld + (long long)i * ld + j] = tf32_round(0.5f * X2[p] - 0.125f * X4[p]);
 }
 
 // X^2 split for the X^2 X^2 product (symmetric operand)
@@ -215,15 +281,19 @@ __global__ void x2_split_kernel(const float *X2, int n, long long ld, float *hi)
     hi[(long long)b * n * ld + (long long)i * ld + j] = tf32_round(X2[(long long)b * n * n + (long long)i * n + j]);
 }
 
-__global__ void add_split_kernel(const float *vthi, const float *vtlo, const float *FV, const float *FtV, int n,
+// (V E)^T = V^T - X V^T + h V^T and V^T <- V^T + X V^T + h V^T, in FP32, re-split;
+// XV = X V^T (split-TF32 product), HV = h V^T (TF32 product), both n x n.
+__global__ void add_split_kernel(const float *vthi, const float *vtlo, const float *XV, const float *HV, int n,
                                  long long ld, float *VEt_hi, float *VEt_lo, float *VThi, float *VTlo, float *VT) {
     const int b = blockIdx.z;
     const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
     if (i >= n || j >= n) return;
     const long long o = (long long)b * n * ld + (long long)i * ld + j;
+    const long long p = (long long)b * n * n + (long long)i * n + j;
     const float v = vthi[o] + vtlo[o];
-    const float ve = v + (FtV[o] + VEt_lo[o]);                       // (V E)^T = V^T + Ft V^T
-    const float vn = v + FV[(long long)b * n * n + (long long)i * n + j];   // V^T <- V^T + F V^T
+    const float xv = XV[p], hv = HV[p];
+    const float ve = v + (hv - xv);
+    const float vn = v + (hv + xv);
     float h, l;
     split_tf32(ve, h, l);
     VEt_hi[o] = h;
@@ -231,10 +301,8 @@ __global__ void add_split_kernel(const float *vthi, const float *vtlo, const flo
     split_tf32(vn, h, l);
     VThi[o] = h;
     VTlo[o] = l;
-    if (VT) VT[(long long)b * n * n + (long long)i * n + j] = vn;
+    if (VT) VT[p] = vn;
 }
-
-
 
 __global__ void hilo_store_kernel(const float *hi, const float *lo, int n, long long ld, float *out) {
     const int b = blockIdx.z;
@@ -261,12 +329,16 @@ struct SvdWS {
     float *Vhi = nullptr, *Vlo = nullptr;            // V = (V^T)^T split
     float *Khi = nullptr, *Klo = nullptr, *T1 = nullptr, *T1hi = nullptr, *T1lo = nullptr, *Kt = nullptr;
     float *X = nullptr, *Xneg = nullptr, *X2 = nullptr, *F = nullptr, *Ft = nullptr, *VEt = nullptr;
+    unsigned *xmax = nullptr;
+    int *mflag = nullptr;
+    double *rsums = nullptr;     // [B][2] range check sums (m > n)
     bool mixed = false;
+    int n_mixed_fallback = 0;    // set by svd_forward
 
     template <class C>
     void carve(C &cv, int B, int m, int n, const psvd_opts &o) {
-        mixed = o.precision == PSVD_PREC_MIXED;
-        pw.carve(cv, B, m, n, polar_kcap(o), mixed);
+        mixed = o.precision != PSVD_PREC_FP32;
+        pw.carve(cv, B, m, n, polar_kcap(o), o.precision);
         ew.carve(cv, B, n, eigh_groups(B, n));
         const long long B64 = B, ld = pad_ld(n), nn = (long long)n * ld;
         S = cv.template take<float>(B64 * n);
@@ -293,6 +365,9 @@ struct SvdWS {
             F = cv.template take<float>(B64 * nn);
             Ft = cv.template take<float>(B64 * nn);
             VEt = cv.template take<float>(B64 * nn * 2);
+            xmax = cv.template take<unsigned>(B64);
+            mflag = cv.template take<int>(B64);
+            rsums = cv.template take<double>(B64 * 2);
         }
     }
 };
@@ -323,6 +398,7 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
     PolarWS &p = w.pw;
     const int B = p.B, m = p.m, n = p.n;
     const long long ld = pad_ld(n), nn = (long long)n * ld;
+    if (cudaMemsetAsync(w.any, 0, sizeof(int) * 4, st)) return PSVD_ERR_CUDA;
     if (int rc = polar_forward(A, nullptr, nullptr, true, p, o, info, st)) return rc;
     if (int rc = eigh_forward(p.Hsym, Sout, nullptr, w.ew, st)) return rc;
     if (cudaMemcpyAsync(w.S, Sout, sizeof(float) * (size_t)B * n, cudaMemcpyDeviceToDevice, st)) return PSVD_ERR_CUDA;
@@ -334,6 +410,18 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
         SplitOut vo;
         vo.hi = w.Vhi; vo.lo = w.Vlo; vo.ld = ld; vo.bstride = nn;
         if (prepare_operand(vthi, ld, nn, B, n, n, true, 1.f, nullptr, vo, st)) return PSVD_ERR_CUDA;
+        if (m > n) {
+            // range check: W Hhat against A, with Hhat^T split into Khi/Klo for the B operand
+            SplitOut ho;
+            ho.hi = w.Khi; ho.lo = w.Klo; ho.ld = ld; ho.bstride = nn;
+            if (prepare_operand(p.Hraw, n, (long long)n * n, B, n, n, true, 1.f, nullptr, ho, st)) return PSVD_ERR_CUDA;
+            if (cudaMemsetAsync(w.rsums, 0, sizeof(double) * 2 * (size_t)B, st)) return PSVD_ERR_CUDA;
+            EpiRange er;
+            er.m = m; er.n = n; er.A = A; er.sums = w.rsums;
+            if (int rc = gemm3(p.Xhi[0], p.Xlo[0], m, n, p.ldn, (long long)m * p.ldn, w.Khi, w.Klo, n, ld, nn, B,
+                               PREC_TF32X3, er, p.err, st))
+                return rc;
+        }
         skewT_kernel<<<g16, b16, 0, st>>>(p.Hraw, n, w.Khi, w.Klo, ld);     // K^T, K = skew(Hhat)
         count_launch(1);
         // T1 = V^T K   (B operand B[j][k] = K[k][j] = K^T[j][k])
@@ -345,9 +433,13 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
         // Ktilde = T1 V   (B operand B[j][k] = V[k][j] = V^T[j][k])
         EpiStore e2 = epi_store_plain(w.Kt, n, (long long)n * n, n, n);
         if (int rc = gemm3(w.T1hi, w.T1lo, n, n, ld, nn, vthi, vtlo, n, ld, nn, B, PREC_TF32X3, e2, p.err, st)) return rc;
-        corr_x_kernel<<<g16, b16, 0, st>>>(w.Kt, w.S, n, w.X, w.Xneg, ld);
+        if (cudaMemsetAsync(w.xmax, 0, sizeof(unsigned) * (size_t)B, st)) return PSVD_ERR_CUDA;
+        corr_x_kernel<<<g16, b16, 0, st>>>(w.Kt, w.S, n, w.X, w.Ft, w.Xneg, ld, w.xmax);   // X_lo in Ft
+        mixed_flag_kernel<<<(B + 127) / 128, 128, 0, st>>>(w.xmax, m > n ? w.rsums : nullptr, B,
+                                                           (float)PSVD_MIXED_CORR_MAX, (float)PSVD_MIXED_RANGE_MAX,
+                                                           w.mflag, w.any + 1, info);
         sigma_refresh_kernel<<<dim3((n + 7) / 8, B), 256, 0, st>>>(w.X, w.S, n, ld, Sout, nullptr);
-        count_launch(2);
+        count_launch(3);
         // X^2 = X X   (B operand B[j][k] = X[k][j] = -X[j][k])
         EpiStore e3 = epi_store_plain(w.X2, n, (long long)n * n, n, n);
         if (int rc = gemm3(w.X, nullptr, n, n, ld, nn, w.Xneg, nullptr, n, ld, nn, B, PREC_TF32, e3, p.err, st)) return rc;
@@ -356,28 +448,22 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
         count_launch(1);
         EpiStore e3b = epi_store_plain(w.T1, n, (long long)n * n, n, n);
         if (int rc = gemm3(w.T1hi, nullptr, n, n, ld, nn, w.T1hi, nullptr, n, ld, nn, B, PREC_TF32, e3b, p.err, st)) return rc;
-        corr_f_kernel<<<g16, b16, 0, st>>>(w.X2, w.T1, w.X, n, ld, w.F, w.Ft);
+        corr_h_kernel<<<g16, b16, 0, st>>>(w.X2, w.T1, n, ld, w.F);                 // h in F
         count_launch(1);
-        // Ft V^T (kept split in VEt) and F V^T (in T1); B operand B[j][k] = V^T[k][j] = V[j][k]
+        // X V^T (split-TF32, into T1) and h V^T (TF32, into Kt); B operand B[j][k] = V^T[k][j] = V[j][k]
         float *VEt_hi = w.VEt, *VEt_lo = w.VEt + (long long)B * nn;
-        EpiStore e4;
-        memset(&e4, 0, sizeof(e4));
-        e4.rows = n; e4.cols = n; e4.alpha = 1.f;
-        e4.hi = VEt_hi; e4.lo = VEt_lo; e4.ldh = ld; e4.bsh = nn;
-        if (int rc = gemm3(w.Ft, nullptr, n, n, ld, nn, w.Vhi, nullptr, n, ld, nn, B, PREC_TF32, e4, p.err, st)) return rc;
-        EpiStore e5 = epi_store_plain(w.T1, n, (long long)n * n, n, n);
+        EpiStore e4 = epi_store_plain(w.T1, n, (long long)n * n, n, n);
+        if (int rc = gemm3(w.X, w.Ft, n, n, ld, nn, w.Vhi, w.Vlo, n, ld, nn, B, PREC_TF32X3, e4, p.err, st)) return rc;
+        EpiStore e5 = epi_store_plain(w.Kt, n, (long long)n * n, n, n);
         if (int rc = gemm3(w.F, nullptr, n, n, ld, nn, w.Vhi, nullptr, n, ld, nn, B, PREC_TF32, e5, p.err, st)) return rc;
-        // (V E)^T = V^T + Ft V^T and V^T <- V^T + F V^T, in FP32, re-split
-        add_split_kernel<<<g16, b16, 0, st>>>(vthi, vtlo, w.T1, VEt_hi, n, ld, VEt_hi, VEt_lo, w.ew.VThi, w.ew.VTlo,
+        add_split_kernel<<<g16, b16, 0, st>>>(vthi, vtlo, w.T1, w.Kt, n, ld, VEt_hi, VEt_lo, w.ew.VThi, w.ew.VTlo,
                                               VT);
         count_launch(1);
         bu_hi = VEt_hi;
         bu_lo = VEt_lo;
     }
     // U = W (V E), with the column norms of Algorithm 1 step 7
-    if (cudaMemsetAsync(w.colss, 0, sizeof(float) * (size_t)B * n, st) ||
-        cudaMemsetAsync(w.any, 0, sizeof(int) * 4, st))
-        return PSVD_ERR_CUDA;
+    if (cudaMemsetAsync(w.colss, 0, sizeof(float) * (size_t)B * n, st)) return PSVD_ERR_CUDA;
     {
         EpiColNorm e;
         e.m = m; e.n = n; e.U = U; e.colss = w.colss;
@@ -391,9 +477,11 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
     }
     qr_flag_kernel<<<B, 256, 0, st>>>(w.colss, n, o.eps_qr, w.flag, w.any);
     count_launch(1);
-    int nflag = 0;
-    if (cudaMemcpyAsync(&nflag, w.any, sizeof(int), cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
+    int counts[2] = {0, 0};      // QR fallbacks, mixed-precision fallbacks
+    if (cudaMemcpyAsync(counts, w.any, sizeof(counts), cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
         return PSVD_ERR_CUDA;
+    w.n_mixed_fallback = w.mixed ? counts[1] : 0;
+    const int nflag = counts[0];
     if (nflag > 0) {
         QrParams q;
         q.U = U; q.UT = w.UT; q.tau = w.qtau; q.beta = w.qbeta; q.flag = w.flag; q.bar = w.qbar; q.err = p.err;
@@ -428,13 +516,85 @@ static psvd_opts svd_resolve(const psvd_opts *p) {
     return o;
 }
 
+// The FP32-accurate rerun of the matrices the mixed pass flagged: options of the
+// plain conservative path, and the workspace layout (gathered inputs, outputs, records,
+// index list, then the plain pipeline's own workspace), carved from the start of the
+// same workspace once the mixed pass has finished with it.
+static psvd_opts plain_opts(const psvd_opts &o) {
+    psvd_opts p = o;
+    p.precision = PSVD_PREC_FP32;
+    p.schedule = PSVD_SCHED_CANS;
+    p.lower_bound = nullptr;
+    p.budget = 0;
+    return p;
+}
+struct RerunWS {
+    float *A = nullptr, *U = nullptr, *S = nullptr, *VT = nullptr;
+    psvd_info *info = nullptr;
+    int *idx = nullptr;
+    SvdWS w;
+    template <class C>
+    void carve(C &cv, int F, int m, int n, const psvd_opts &plain) {
+        const long long F64 = F;
+        A = cv.template take<float>(F64 * m * n);
+        U = cv.template take<float>(F64 * m * n);
+        S = cv.template take<float>(F64 * n);
+        VT = cv.template take<float>(F64 * n * n);
+        info = cv.template take<psvd_info>(F64);
+        idx = cv.template take<int>(F64);
+        w.carve(cv, F, m, n, plain);
+    }
+};
+
+static int mixed_fallback(const float *A, float *U, float *S, float *VT, int B, int m, int n, const SvdWS &w,
+                          const psvd_opts &o, void *ws, size_t ws_bytes, psvd_info *info, cudaStream_t st) {
+    std::vector<int> flags(B);
+    PSVD_TRY(cudaMemcpyAsync(flags.data(), w.mflag, sizeof(int) * (size_t)B, cudaMemcpyDeviceToHost, st));
+    PSVD_TRY(cudaStreamSynchronize(st));
+    std::vector<int> idx;
+    for (int b = 0; b < B; ++b)
+        if (flags[b]) idx.push_back(b);
+    const int F = (int)idx.size();
+    if (F == 0) return PSVD_OK;
+    const psvd_opts po = plain_opts(o);
+    Carver cv(ws, ws_bytes);
+    RerunWS r;
+    r.carve(cv, F, m, n, po);
+    if (cv.overflow) return PSVD_ERR_WORKSPACE;
+    const size_t mn = (size_t)m * n, nn = (size_t)n * n;
+    PSVD_TRY(cudaMemcpyAsync(r.idx, idx.data(), sizeof(int) * (size_t)F, cudaMemcpyHostToDevice, st));
+    for (int j = 0; j < F; ++j)
+        PSVD_TRY(cudaMemcpyAsync(r.A + j * mn, A + idx[j] * mn, sizeof(float) * mn, cudaMemcpyDeviceToDevice, st));
+    PSVD_TRY_RC(svd_forward(r.A, r.U, r.S, r.VT, r.w, po, info ? r.info : nullptr, st));
+    for (int j = 0; j < F; ++j) {
+        const size_t b = (size_t)idx[j];
+        PSVD_TRY(cudaMemcpyAsync(U + b * mn, r.U + j * mn, sizeof(float) * mn, cudaMemcpyDeviceToDevice, st));
+        PSVD_TRY(cudaMemcpyAsync(S + b * n, r.S + (size_t)j * n, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+        PSVD_TRY(cudaMemcpyAsync(VT + b * nn, r.VT + j * nn, sizeof(float) * nn, cudaMemcpyDeviceToDevice, st));
+    }
+    if (info) {
+        info_scatter_kernel<<<(F + 127) / 128, 128, 0, st>>>(info, r.info, r.idx, F);
+        count_launch(1);
+        PSVD_TRY(cudaGetLastError());
+    }
+    return PSVD_OK;
+}
+
 extern "C" size_t psvd_svd_workspace_bytes(int64_t batch, int64_t m, int64_t n, const psvd_opts *opts) {
     psvd_opts o = svd_resolve(opts);
     if (batch <= 0 || m <= 0 || n <= 0) return 0;
     Sizer s;
     SvdWS w;
     w.carve(s, (int)batch, (int)m, (int)n, o);
-    return s.used + 256;
+    size_t need = s.used;
+    if (o.precision != PSVD_PREC_FP32) {
+        // room for rerunning every matrix on the FP32-accurate path
+        Sizer s2;
+        RerunWS r;
+        r.carve(s2, (int)batch, (int)m, (int)n, plain_opts(o));
+        need = std::max(need, s2.used);
+    }
+    return need + 256;
 }
 
 extern "C" int psvd_svd_fwd(const float *A, float *U, float *S, float *VT, int64_t batch, int64_t m, int64_t n,
@@ -443,7 +603,8 @@ extern "C" int psvd_svd_fwd(const float *A, float *U, float *S, float *VT, int64
     if (!A || !U || !S || !VT || batch <= 0 || n <= 0 || m < n || batch > 65535 || n > 16384 ||
         (long long)m * n > (1LL << 31))
         return PSVD_ERR_ARG;
-    if (o.precision != PSVD_PREC_FP32 && o.precision != PSVD_PREC_MIXED) return PSVD_ERR_ARG;
+    if (o.precision != PSVD_PREC_FP32 && o.precision != PSVD_PREC_MIXED && o.precision != PSVD_PREC_MIXED_BF16)
+        return PSVD_ERR_ARG;
     if (o.schedule == PSVD_SCHED_LEARNED && !o.lower_bound) return PSVD_ERR_ARG;
     if (int e = check_device()) return e;
     if (ws_bytes < psvd_svd_workspace_bytes(batch, m, n, &o)) return PSVD_ERR_WORKSPACE;
@@ -451,5 +612,9 @@ extern "C" int psvd_svd_fwd(const float *A, float *U, float *S, float *VT, int64
     SvdWS w;
     w.carve(cv, (int)batch, (int)m, (int)n, o);
     if (cv.overflow) return PSVD_ERR_WORKSPACE;
-    return svd_forward(A, U, S, VT, w, o, info, static_cast<cudaStream_t>(stream));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PSVD_TRY_RC(svd_forward(A, U, S, VT, w, o, info, st));
+    if (w.n_mixed_fallback > 0)
+        return mixed_fallback(A, U, S, VT, (int)batch, (int)m, (int)n, w, o, ws, ws_bytes, info, st);
+    return PSVD_OK;
 }

@@ -36,7 +36,7 @@ def test_noalloc_matches_polar_fwd_on_consecutive_calls(precision):
         w_ref, h_ref, info_ref = P.polar(A, opts, return_info=True)
         Wt = torch.empty_like(A)
         Ht = torch.empty(2, 160, 160, device="cuda")
-        info = torch.zeros(2, 9, dtype=torch.int32, device="cuda")
+        info = torch.zeros(2, P.INFO_WORDS, dtype=torch.int32, device="cuda")
         rc = fn(P._ptr(A), P._ptr(Wt), P._ptr(Ht), 2, 200, 160, ctypes.byref(opts), P._ptr(info), P._stream())
         assert rc == 0, P.lib().psvd_last_error()
         torch.cuda.synchronize()
