@@ -185,8 +185,18 @@ def main():
     GVT = torch.from_numpy(rng.standard_normal((N, N)).astype(np.float32)).T.contiguous().to(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
 
-    def make(precision):
-        o = P.make_opts(precision=precision)
+    # learned lower bound: network trained by paper_2609_32505_gb300.train_schedule, probes
+    # drawn once; the features, the network and the bound run inside the timed step
+    from paper_2609_32505_gb300 import train_schedule
+    mlp_params, mlp_margin, nprobe = train_schedule.load(device=dev)
+    Zp = P.rademacher_probes(1, N, nprobe, seed=5, device=dev)
+    Fp = torch.empty(1, 8, device=dev)
+    wsk = P._workspace(L.psvd_sketch_workspace_bytes(1, N, N, nprobe), dev)
+
+    def make(precision, learned=False):
+        lb = torch.full((1,), 0.5, device=dev)
+        o = P.make_opts(precision=precision, schedule=P.SCHED_LEARNED if learned else P.SCHED_CANS,
+                        lower_bound=lb if learned else None)
         U = torch.empty(1, N, N, device=dev)
         S = torch.empty(1, N, device=dev)
         VT = torch.empty(1, N, N, device=dev)
@@ -194,11 +204,16 @@ def main():
         info = torch.zeros(1, P.INFO_WORDS, dtype=torch.int32, device=dev)
         wsf = P._workspace(L.psvd_svd_workspace_bytes(1, N, N, ctypes.byref(o)), dev)
         wsb = P._workspace(L.psvd_svd_bwd_workspace_bytes(1, N, N), dev)
-        return o, U, S, VT, dA, info, wsf, wsb
+        return o, U, S, VT, dA, info, wsf, wsb, (lb if learned else None)
 
     def step(bufs, a_dev):
-        o, U, S, VT, dA, info, wsf, wsb = bufs
+        o, U, S, VT, dA, info, wsf, wsb, lb = bufs
         st = P._stream()
+        if lb is not None:
+            P._check(L.psvd_sketch_features(P._ptr(a_dev), P._ptr(Zp), nprobe, P._ptr(Fp), 1, N, N, P._ptr(wsk),
+                                            wsk.numel(), st), "sketch")
+            P._check(L.psvd_mlp_lower_bound(P._ptr(mlp_params), P._ptr(Fp), P._ptr(lb), 1, float(mlp_margin), st),
+                     "lower_bound")
         P._check(L.psvd_svd_fwd(P._ptr(a_dev), P._ptr(U), P._ptr(S), P._ptr(VT), 1, N, N, ctypes.byref(o),
                                 P._ptr(wsf), wsf.numel(), P._ptr(info), st), "svd_fwd")
         P._check(L.psvd_svd_bwd(P._ptr(a_dev), P._ptr(U), P._ptr(S), P._ptr(VT), P._ptr(GU), P._ptr(GS),
@@ -216,7 +231,7 @@ def main():
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
 
-    mixed = make(P.PREC_MIXED)
+    mixed = make(P.PREC_MIXED, learned=True)
     plain = make(P.PREC_FP32)
     for _ in range(max(3, args.warmup)):
         step(mixed, A)
@@ -253,6 +268,19 @@ def main():
                 "ortho_v": float(torch.linalg.matrix_norm(vt @ vt.T - eye) / N ** 0.5)}
 
     acc_m, acc_p = accuracy(mixed), accuracy(plain)
+    sched_m = {"steps": [info_m["steps_bf16"], info_m["steps_tf32"], info_m["steps_3xtf32"]],
+               "lower_bound": float(mixed[8][0]), "sched_fallback": info_m["sched_fallback"]}
+
+    # the BF16-first ladder (PSVD_PREC_MIXED_BF16), reported beside the headline
+    bf16 = make(P.PREC_MIXED_BF16, learned=True)
+    for _ in range(2):
+        step(bf16, A)
+    t_bf16 = [timed_one(bf16) for _ in range(3)]
+    info_b = P.info_dict(bf16[5])[0]
+    bf16_report = {"median_ms": float(np.median(t_bf16)), "accuracy": accuracy(bf16),
+                   "corr_max": info_b["corr_max"], "prec_fallback": info_b["prec_fallback"],
+                   "polar_steps": [info_b["steps_bf16"], info_b["steps_tf32"], info_b["steps_3xtf32"]]}
+    del bf16
     sig_err = acc_m["sigma_err_rel_smax"]
 
     # roofline: CUDA events around each launch of the tridiagonalization (the dominant
@@ -326,7 +354,11 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": f"SVD fwd+bwd of one {N}x{N} fp32 matrix A = Q1 diag(s) Q2^T, "
                                        f"s_i = {KAPPA:g}^((n-i)/(n-1)), eps=1e-8, kreg Algorithm 4",
-                           "path": "mixed: BF16->TF32->split-TF32 polish + eigenbasis correction, CANS delta=0.99",
+                           "path": "mixed: learned lower bound (sketch + MLP kernels) -> greedy cubics, TF32 steps "
+                                   "-> split-TF32 polish, eigenbasis correction; plain: conservative CANS "
+                                   "(delta=0.99), split-TF32 throughout",
+                           "schedule_mixed": sched_m,
+                           "bf16_ladder": bf16_report,
                            "plain_ms": ms_plain, "speedup_mixed_vs_plain": ms_plain / ms_mixed,
                            "median_ms": {"mixed": float(np.median(t_mixed)), "plain": float(np.median(t_plain))},
                            "accuracy_plain": acc_p,

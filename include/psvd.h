@@ -195,6 +195,13 @@ size_t psvd_sketch_workspace_bytes(int64_t batch, int64_t m, int64_t n, int64_t 
 #define PSVD_MLP_NPARAMS (64 * 8 + 64 + 64 * 64 + 64 + 64 + 1)
 int psvd_mlp_fwd(const float *params, const float *F, float *Y, int64_t nb, void *stream);
 
+/* psvd_mlp_lower_bound -- the lower bound the learned schedule takes (opts.lower_bound):
+ *   LB[i] = margin * exp(y_i), y = psvd_mlp_fwd(params, F), clamped to [1e-12, 0.999].
+ *   The network predicts log sigma_min(X0); margin (> 0, from a held-out quantile of the
+ *   over-prediction) makes it a lower bound for most matrices, and the conservative rerun
+ *   covers the rest.  LB: DEVICE, nb floats out. */
+int psvd_mlp_lower_bound(const float *params, const float *F, float *LB, int64_t nb, float margin, void *stream);
+
 /* psvd_mlp_train_step -- one Adam step on 0.5 mean (y - target)^2 over the batch.
  *   grads (PSVD_MLP_NPARAMS floats), m1/m2 (Adam moments, same size) are DEVICE
  *   buffers; `step` is the 1-based Adam step count.  loss: DEVICE float out (may be NULL). */

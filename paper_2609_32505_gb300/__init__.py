@@ -83,6 +83,7 @@ def lib():
         "psvd_sketch_workspace_bytes": (sz, [i64, i64, i64, i64]),
         "psvd_sketch_features": (ctypes.c_int, [vp, vp, i64, vp, i64, i64, i64, vp, sz, vp]),
         "psvd_mlp_fwd": (ctypes.c_int, [vp, vp, vp, i64, vp]),
+        "psvd_mlp_lower_bound": (ctypes.c_int, [vp, vp, vp, i64, ctypes.c_float, vp]),
         "psvd_mlp_grad": (ctypes.c_int, [vp, vp, vp, i64, vp, vp, vp]),
         "psvd_mlp_train_step": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_int, vp, vp]),
         "psvd_profile_read": (ctypes.c_int, [vp]),
@@ -380,9 +381,13 @@ def mlp_calibrate(params: torch.Tensor, feats: torch.Tensor, target: torch.Tenso
 
 
 def predict_lower_bound(a: torch.Tensor, params: torch.Tensor, margin: float = 0.5, probes: int = 8,
-                        seed: int = 0) -> torch.Tensor:
-    """Per-matrix lower bound of sigma_min(X0) for the learned schedule: margin * exp(MLP(features))."""
+                        seed: int = 0, z: torch.Tensor | None = None) -> torch.Tensor:
+    """Per-matrix lower bound of sigma_min(X0) for the learned schedule: margin * exp(MLP(features)),
+    all on the device (sketch kernels, then psvd_mlp_lower_bound).  `z`: probes drawn in advance."""
     A, _ = _batched(a)
-    Z = rademacher_probes(A.shape[0], A.shape[2], probes, seed, A.device)
-    y = mlp_forward(params, sketch_features(A, Z))
-    return (torch.exp(y) * margin).clamp(1e-12, 0.999).contiguous()
+    Z = z if z is not None else rademacher_probes(A.shape[0], A.shape[2], probes, seed, A.device)
+    F = sketch_features(A, Z)
+    lb = torch.empty(F.shape[0], device=F.device, dtype=torch.float32)
+    _check(lib().psvd_mlp_lower_bound(_ptr(params), _ptr(F), _ptr(lb), F.shape[0], float(margin), _stream()),
+           "psvd_mlp_lower_bound")
+    return lb

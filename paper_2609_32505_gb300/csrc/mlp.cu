@@ -286,6 +286,25 @@ extern "C" int psvd_mlp_fwd(const float *params, const float *F, float *Y, int64
     return PSVD_OK;
 }
 
+// Lower bound of sigma_min(X0) from the network's log prediction: margin * exp(y), kept
+// inside [1e-12, 0.999] (the schedule needs 0 < l < 1).
+__global__ void lower_bound_kernel(float *Y, int nb, float margin) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nb) Y[i] = fminf(fmaxf(margin * expf(Y[i]), 1e-12f), 0.999f);
+}
+
+extern "C" int psvd_mlp_lower_bound(const float *params, const float *F, float *LB, int64_t nb, float margin,
+                                    void *stream) {
+    if (!params || !F || !LB || nb <= 0 || !(margin > 0.f)) return PSVD_ERR_ARG;
+    if (int e = check_device()) return e;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    mlp_fwd_kernel<<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(params, F, (int)nb, LB);
+    lower_bound_kernel<<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(LB, (int)nb, margin);
+    count_launch(2);
+    PSVD_TRY(cudaGetLastError());
+    return PSVD_OK;
+}
+
 extern "C" int psvd_mlp_grad(const float *params, const float *F, const float *target, int64_t nb, float *grads,
                              float *loss, void *stream) {
     if (!params || !F || !target || !grads || nb <= 0) return PSVD_ERR_ARG;

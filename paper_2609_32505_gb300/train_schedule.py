@@ -1,0 +1,104 @@
+"""Trains the lower-bound network of the learned polynomial schedule on the GPU.
+
+    python -m paper_2609_32505_gb300.train_schedule [--out paper_2609_32505_gb300/schedule_mlp.npz]
+
+Training data are spectra the method itself produces: seeded matrices from the three
+families of the learned-schedule study (geometric spectra with kappa in [1e1, 1e6], power
+laws i^-p with p in [0.3, 1.5], rank 64 plus 1e-4 Gaussian noise) at several sizes, whose
+smallest singular value and normalization scale come from the library's own FP32-accurate
+svd_fwd.  The target is log sigma_min(X0), X0 = M / sqrt(||M||_1 ||M||_inf); the features
+are the eight sketch features (psvd_sketch_features) with seeded Rademacher probes.  The
+network is fitted with the library's Adam kernels (mlp_fit), and the safety margin is a
+quantile of the over-prediction on held-out matrices.  The file holds the parameters, the
+margin, the number of probes and the fit statistics.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import paper_2609_32505_gb300 as P  # noqa: E402
+import workloads as W  # noqa: E402
+
+DEFAULT_OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "schedule_mlp.npz")
+PROBES = 8
+
+
+def family_batch(seeds, n, device):
+    """Matrices of the three families (seeded) as one (len(seeds), n, n) FP32 batch."""
+    out = torch.empty(len(seeds), n, n, device=device)
+    for i, s in enumerate(seeds):
+        fam, spec = W.schedule_family(int(s), n)
+        a = W.torch_constructed(50_000 + int(s), n, n, spec, device=device)[0]
+        if fam == 2:
+            g = torch.Generator(device="cpu")
+            g.manual_seed(60_000 + int(s))
+            a = a + 1e-4 * torch.randn(n, n, generator=g).to(device)
+        out[i] = a
+    return out
+
+
+def features_and_labels(seeds, n, device, chunk=32):
+    feats, labels = [], []
+    for c in range(0, len(seeds), chunk):
+        sd = seeds[c:c + chunk]
+        A = family_batch(sd, n, device)
+        _, s, _, info = P.svd_fwd(A, P.make_opts(), return_info=True)
+        scale = torch.tensor([i["scale"] for i in info], device=device)
+        labels.append(torch.log(s[:, -1].clamp_min(1e-30) / scale))
+        Z = P.rademacher_probes(len(sd), n, PROBES, seed=int(sd[0]), device=device)
+        feats.append(P.sketch_features(A, Z))
+        del A
+    return torch.cat(feats), torch.cat(labels)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=DEFAULT_OUT)
+    ap.add_argument("--sizes", default="256:1024,512:768,1024:256")
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--quantile", type=float, default=0.95)
+    a = ap.parse_args(argv)
+    dev = torch.device("cuda")
+    P.lib()
+    F, Y = [], []
+    seed = 10_000
+    for item in a.sizes.split(","):
+        n, cnt = (int(x) for x in item.split(":"))
+        f, y = features_and_labels(list(range(seed, seed + cnt)), n, dev)
+        seed += cnt
+        F.append(f)
+        Y.append(y)
+        print(f"n={n}: {cnt} matrices", flush=True)
+    F, Y = torch.cat(F), torch.cat(Y)
+    g = torch.Generator(device="cpu")
+    g.manual_seed(1)
+    perm = torch.randperm(F.shape[0], generator=g).to(dev)
+    F, Y = F[perm].contiguous(), Y[perm].contiguous()
+    nh = max(1, F.shape[0] // 5)                     # held out for the margin
+    params, curve = P.mlp_fit(F[nh:], Y[nh:], steps=a.steps, lr=3e-3, batch=256, seed=0)
+    margin = P.mlp_calibrate(params, F[:nh], Y[:nh], quantile=a.quantile)
+    resid = (P.mlp_forward(params, F[:nh]) - Y[:nh]).abs()
+    np.savez(a.out, params=params.cpu().numpy().astype(np.float32), margin=np.float32(margin),
+             probes=np.int32(PROBES), loss_first=np.float32(curve[0]), loss_last=np.float32(curve[-1]),
+             heldout_median_abs=np.float32(resid.median().item()), count=np.int32(F.shape[0]))
+    print(f"trained on {F.shape[0] - nh}, held out {nh}: loss {curve[0]:.3f} -> {curve[-1]:.4f}, "
+          f"held-out median |log error| {resid.median().item():.3f}, margin {margin:.3f} -> {a.out}")
+
+
+def load(path: str = DEFAULT_OUT, device="cuda"):
+    """(params on `device`, margin, probes) from a file written by main()."""
+    d = np.load(path)
+    return torch.from_numpy(d["params"]).to(device), float(d["margin"]), int(d["probes"])
+
+
+if __name__ == "__main__":
+    main()
