@@ -3,7 +3,8 @@
 //     one group barrier per reflector; the row that the next reflector is built from
 //     is left un-updated and corrected on the fly, so the rank-2 update of step k and
 //     the matrix-vector product of step k+1 touch only rows owned by the same warp).
-//  2. Eigenvalues of T by Sturm-count multisection (FP32, on T scaled to unit norm).
+//  2. Eigenvalues of T by Sturm-count multisection (FP32, on T scaled to unit norm);
+//     eigenvalues with close neighbours refined by FP64 multisection.
 //  3. Eigenvectors of T by inverse iteration (FP64, one thread per eigenvalue,
 //     partially pivoted tridiagonal LU, operands streamed through shared memory),
 //     Rayleigh quotients, modified Gram-Schmidt inside clusters of close eigenvalues.
@@ -376,12 +377,95 @@ __global__ void tri_bisect_kernel(const double *D, const double *E, int n, doubl
     lam[(long long)b * n + i] = 0.5 * ((double)lo + (double)hi) * tn;
 }
 
+// ------------------------------------------------------------ refinement (FP64)
+// FP64 Sturm count of T - x I (T unscaled), pivots floored at pivmin.
+PSVD_DEV int sturm_count64(const double *__restrict__ d, const double *__restrict__ e, int n, double x,
+                           double pivmin) {
+    int c = 0;
+    double q = d[0] - x;
+    if (fabs(q) < pivmin) q = -pivmin;
+    c += q < 0.0;
+    for (int t = 1; t < n; ++t) {
+        const double et = e[t - 1];
+        q = (d[t] - x) - (et * et) / q;
+        if (fabs(q) < pivmin) q = -pivmin;
+        c += q < 0.0;
+    }
+    return c;
+}
+
+// Eigenvalues whose FP32 neighbours are closer than `near` * ||T|| are refined in FP64 by
+// 9-way multisection (8 lanes per eigenvalue) from a bracket around the FP32 value, down
+// to ~4 u_64 ||T||.  With such shifts inverse iteration separates gaps down to ~1e-12 ||T||
+// by itself, so the Gram-Schmidt of close eigenvalues stays for near-exact multiplicities.
+__global__ void tri_refine_kernel(const double *D, const double *E, int n, const double *tnorm, double near,
+                                  double *lam) {
+    const int b = blockIdx.y;
+    const int grp = threadIdx.x >> 3, l = threadIdx.x & 7;
+    const int i = blockIdx.x * (blockDim.x >> 3) + grp;     // descending index
+    const double *d = D + (long long)b * n, *e = E + (long long)b * n;
+    double *lb = lam + (long long)b * n;
+    const double tn = tnorm[b];
+    bool active = i < n && n > 1 && tn > 0.0;
+    double mid = 0.0;
+    if (active) {
+        mid = lb[i];
+        double g = 1e300;
+        if (i > 0) g = fmin(g, lb[i - 1] - mid);
+        if (i + 1 < n) g = fmin(g, mid - lb[i + 1]);
+        active = g < near * tn;
+    }
+    const bool refined = active;
+    const int j = n - 1 - i;                                 // ascending index
+    const double pivmin = fmax(tn * 1e-290, 1e-300);
+    const double stop = 4.0 * DBL_EPSILON * tn;
+    double w = 64.0 * FLT_EPSILON * tn;
+    double lo = mid - w, hi = mid + w;
+    const unsigned gshift = (threadIdx.x & 31) & ~7u;
+    // a bracket with count(lo) <= j < count(hi), widened if the FP32 value was off
+    for (int tries = 0; tries < 6; ++tries) {
+        bool need = false;
+        if (active) {
+            const double x = l == 0 ? lo : hi;
+            const int c = l < 2 ? sturm_count64(d, e, n, x, pivmin) : 0;
+            const bool ok = l == 0 ? c <= j : (l == 1 ? c > j : true);
+            const unsigned bad = (__ballot_sync(0xffffffffu, !ok) >> gshift) & 0x3u;
+            need = bad != 0;
+        } else {
+            __ballot_sync(0xffffffffu, false);
+        }
+        if (!__any_sync(0xffffffffu, need)) break;
+        if (need) { w *= 16.0; lo = mid - w; hi = mid + w; }
+    }
+    for (int round = 0; round < 24; ++round) {
+        const bool go = active && hi - lo > stop;
+        if (!__any_sync(0xffffffffu, go)) break;
+        const double width = hi - lo;
+        const double x = lo + width * ((double)(l + 1) / 9.0);
+        const bool le = go && sturm_count64(d, e, n, x, pivmin) <= j;
+        const unsigned bits = (__ballot_sync(0xffffffffu, le) >> gshift) & 0xFFu;
+        if (go) {
+            const int k = __popc(bits);
+            const double nlo = k > 0 ? lo + width * ((double)k / 9.0) : lo;
+            const double nhi = k < 8 ? lo + width * ((double)(k + 1) / 9.0) : hi;
+            if (nlo <= lo && nhi >= hi) active = false;
+            else { lo = nlo; hi = nhi; }
+        }
+    }
+    if (refined && l == 0) lb[i] = 0.5 * (lo + hi);
+}
+
 // ------------------------------------------------------------ inverse iteration (FP64)
 PSVD_DEV double hash_unit(unsigned a, unsigned b) {
     unsigned h = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u) * 0x85EBCA77u;
     h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
     return (double)h * (2.0 / 4294967296.0) - 1.0;
 }
+
+// Eigenvalues closer than kRefineNear ||T|| (by their FP32 values) are refined in FP64;
+// Gram-Schmidt then runs only inside groups closer than kClusterTol ||T||.
+constexpr double kRefineNear = 1e-5;
+constexpr double kClusterTol = 1e-12;
 
 struct InvitParams {
     const double *D, *E, *tn;
@@ -829,7 +913,13 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
         PSVD_TRY(cudaGetLastError());
         count_launch(1);
     }
-    // keep the bisection values for cluster detection
+    {
+        dim3 g((n + 31) / 32, B);       // 32 eigenvalues x 8 lanes per block
+        tri_refine_kernel<<<g, 256, 0, st>>>(w.d, w.e, n, tn, kRefineNear, w.lam);
+        PSVD_TRY(cudaGetLastError());
+        count_launch(1);
+    }
+    // keep the eigenvalues for cluster detection
     double *bis = reinterpret_cast<double *>(w.S);   // B*n doubles (S holds B*n*kWY floats)
     PSVD_TRY(cudaMemcpyAsync(bis, w.lam, sizeof(double) * (size_t)B * n, cudaMemcpyDeviceToDevice, st));
     // 3. eigenvectors of T, chunk by chunk (chunks hold whole matrices)
@@ -842,7 +932,7 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
         P.xs = w.xs; P.u0 = w.u0; P.u1 = w.u1; P.u2 = w.u2; P.lm = w.lm; P.piv = w.piv;
         P.n = n; P.first = b0 * n; P.count = nb * n; P.stride = w.chunk;
         tri_invit_kernel<<<(P.count + 31) / 32, 32, kIvSmem, st>>>(P);
-        tri_cluster_kernel<<<nb, 256, 0, st>>>(P, bis, 1e-5);
+        tri_cluster_kernel<<<nb, 256, 0, st>>>(P, bis, kClusterTol);
         dim3 g((n + 31) / 32, (n + 31) / 32, nb), blk(32, 8);
         zt_store_kernel<<<g, blk, 0, st>>>(w.xs, w.chunk, n, b0, b0 * n, w.VThi, w.VTlo, ldn);
         PSVD_TRY(cudaGetLastError());

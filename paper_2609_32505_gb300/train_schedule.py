@@ -4,7 +4,8 @@
 
 Training data are spectra the method itself produces: seeded matrices from the three
 families of the learned-schedule study (geometric spectra with kappa in [1e1, 1e6], power
-laws i^-p with p in [0.3, 1.5], rank 64 plus 1e-4 Gaussian noise) at several sizes, whose
+laws i^-p with p in [0.3, 1.5], rank 64 plus 1e-4 Gaussian noise) at sizes 256 to 4096
+(Haar orthogonal factors from a device QR of seeded Gaussians), whose
 smallest singular value and normalization scale come from the library's own FP32-accurate
 svd_fwd.  The target is log sigma_min(X0), X0 = M / sqrt(||M||_1 ||M||_inf); the features
 are the eight sketch features (psvd_sketch_features) with seeded Rademacher probes.  The
@@ -32,21 +33,39 @@ DEFAULT_OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "schedule
 PROBES = 8
 
 
+def _orthonormal(gen, n, device):
+    """Haar orthogonal n x n: Q of the device QR of a Gaussian, signs fixed by diag(R) > 0.
+    FP32 (GB300's FP64 rate is low, and the labels come from svd_fwd on the matrix as built)."""
+    g = torch.randn(n, n, generator=gen, dtype=torch.float32).to(device)
+    q, r = torch.linalg.qr(g)
+    d = torch.sign(torch.diagonal(r))
+    return q * torch.where(d == 0, torch.ones_like(d), d)[None, :]
+
+
 def family_batch(seeds, n, device):
     """Matrices of the three families (seeded) as one (len(seeds), n, n) FP32 batch."""
     out = torch.empty(len(seeds), n, n, device=device)
     for i, s in enumerate(seeds):
         fam, spec = W.schedule_family(int(s), n)
-        a = W.torch_constructed(50_000 + int(s), n, n, spec, device=device)[0]
+        if n >= 2048 and fam == 2:
+            # rank 64 + noise gives one cluster of ~n nearly equal eigenvalues, whose
+            # single-block Gram-Schmidt in the eigensolver is too slow at this size;
+            # the geometric family stands in for it
+            spec = W.kappa_spectrum(n, 10.0 ** (1 + 5 * ((int(s) * 7919) % 1000) / 1000.0))
+            fam = 0
+        gen = torch.Generator()
+        gen.manual_seed(50_000 + int(s))
+        q1, q2 = _orthonormal(gen, n, device), _orthonormal(gen, n, device)
+        sp = torch.as_tensor(np.ascontiguousarray(spec), dtype=torch.float32, device=device)
+        a = (q1 * sp[None, :]) @ q2.T
         if fam == 2:
-            g = torch.Generator(device="cpu")
-            g.manual_seed(60_000 + int(s))
-            a = a + 1e-4 * torch.randn(n, n, generator=g).to(device)
+            a = a + 1e-4 * torch.randn(n, n, generator=gen).to(device)
         out[i] = a
     return out
 
 
-def features_and_labels(seeds, n, device, chunk=32):
+def features_and_labels(seeds, n, device):
+    chunk = max(1, min(32, (1 << 24) // (n * n)))
     feats, labels = [], []
     for c in range(0, len(seeds), chunk):
         sd = seeds[c:c + chunk]
@@ -63,7 +82,7 @@ def features_and_labels(seeds, n, device, chunk=32):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=DEFAULT_OUT)
-    ap.add_argument("--sizes", default="256:1024,512:768,1024:256")
+    ap.add_argument("--sizes", default="256:768,512:512,1024:256,2048:96,4096:32")
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--quantile", type=float, default=0.95)
     a = ap.parse_args(argv)
@@ -77,7 +96,7 @@ def main(argv=None):
         seed += cnt
         F.append(f)
         Y.append(y)
-        print(f"n={n}: {cnt} matrices", flush=True)
+        print(f"n={n}: {cnt} matrices, labels in [{y.min().item():.2f}, {y.max().item():.2f}]", flush=True)
     F, Y = torch.cat(F), torch.cat(Y)
     g = torch.Generator(device="cpu")
     g.manual_seed(1)

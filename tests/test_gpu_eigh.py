@@ -76,3 +76,21 @@ def test_eigh_diagonal_and_zero():
     np.testing.assert_allclose(s[0], [5, 3, 3, 0, -1], atol=1e-6)
     np.testing.assert_allclose(s[1], 0.0, atol=0)
     assert np.abs(vt[1] @ vt[1].T - np.eye(5)).max() < 1e-6
+
+
+@pytest.mark.parametrize("kappa", [1e3, 1e6])
+def test_eigh_graded_spectrum(kappa):
+    # geometric eigenvalues kappa^(-(i)/(n-1)): the small ones are closer than 1e-5 ||H||
+    # to each other, so their FP32 estimates are refined in FP64 before inverse iteration;
+    # the vectors must come out orthonormal and satisfy H V = V Lambda to FP32 level
+    n = 400
+    rng = W.rng_for(91)
+    q = W.orthonormal(rng, n, n)
+    lam0 = kappa ** (-np.arange(n) / (n - 1))
+    h = ((q * lam0[None, :]) @ q.T).astype(np.float32).astype(np.float64)
+    s, vt = _run(h[None])
+    lam, _ = O.eigh(h)
+    assert np.abs(s[0] - lam).max() <= 2e-6 * np.sqrt(n) / 8
+    V = vt[0].T
+    assert np.abs(V.T @ V - np.eye(n)).max() <= 1e-5
+    assert np.linalg.norm(h @ V - V * s[0][None, :]) <= 1e-5 * np.sqrt(n)

@@ -166,7 +166,7 @@ def torch_constructed(seed: int, m: int, n: int, s, device="cuda", batch: int = 
     import torch
     gen = torch.Generator()
     gen.manual_seed(int(seed))
-    s = torch.as_tensor(np.asarray(s, dtype=np.float64), device=device)
+    s = torch.as_tensor(np.ascontiguousarray(s, dtype=np.float64), device=device)
     if s.dim() == 1:
         s = s[None, :].expand(batch, -1)
     out = torch.empty(batch, m, n, device=device, dtype=torch.float32)
