@@ -238,17 +238,20 @@ def main():
         step(plain, A)
     torch.cuda.synchronize()
 
-    # the two paths alternate step by step, so that both see the same clocks and box state
+    # the two paths alternate step by step, and which one goes first alternates too, so
+    # that both see the same clocks and box state
     t_mixed, t_plain = [], []
     launches = launches_plain = 0
     with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            c0 = P.kernel_launches()
-            t_mixed.append(timed_one(mixed))
-            c1 = P.kernel_launches()
-            t_plain.append(timed_one(plain))
-            launches += c1 - c0                        # over the K timed headline steps
-            launches_plain += P.kernel_launches() - c1
+        for it in range(args.steps):
+            for arm in ((0, 1) if it % 2 == 0 else (1, 0)):
+                c0 = P.kernel_launches()
+                if arm == 0:
+                    t_mixed.append(timed_one(mixed))
+                    launches += P.kernel_launches() - c0   # over the K timed headline steps
+                else:
+                    t_plain.append(timed_one(plain))
+                    launches_plain += P.kernel_launches() - c0
     ms_mixed, ms_plain = float(np.mean(t_mixed)), float(np.mean(t_plain))
     if ws > 1:
         t = torch.tensor([ms_mixed, ms_plain], device=dev)
@@ -361,6 +364,7 @@ def main():
                            "bf16_ladder": bf16_report,
                            "plain_ms": ms_plain, "speedup_mixed_vs_plain": ms_plain / ms_mixed,
                            "median_ms": {"mixed": float(np.median(t_mixed)), "plain": float(np.median(t_plain))},
+                           "step_ms": {"mixed": [round(t, 2) for t in t_mixed], "plain": [round(t, 2) for t in t_plain]},
                            "accuracy_plain": acc_p,
                            "l2": "512 MB buffer written between timed steps",
                            "launches_per_step": {"mixed": launches // max(1, args.steps),

@@ -47,12 +47,6 @@ def family_batch(seeds, n, device):
     out = torch.empty(len(seeds), n, n, device=device)
     for i, s in enumerate(seeds):
         fam, spec = W.schedule_family(int(s), n)
-        if n >= 2048 and fam == 2:
-            # rank 64 + noise gives one cluster of ~n nearly equal eigenvalues, whose
-            # single-block Gram-Schmidt in the eigensolver is too slow at this size;
-            # the geometric family stands in for it
-            spec = W.kappa_spectrum(n, 10.0 ** (1 + 5 * ((int(s) * 7919) % 1000) / 1000.0))
-            fam = 0
         gen = torch.Generator()
         gen.manual_seed(50_000 + int(s))
         q1, q2 = _orthonormal(gen, n, device), _orthonormal(gen, n, device)
