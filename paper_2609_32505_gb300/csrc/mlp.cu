@@ -21,8 +21,11 @@ constexpr int kP_W1 = 0, kP_b1 = kH * kF, kP_W2 = kP_b1 + kH, kP_b2 = kP_W2 + kH
               kP_b3 = kP_W3 + kH, kNP = kP_b3 + 1;
 static_assert(kNP == PSVD_MLP_NPARAMS, "parameter layout");
 
+constexpr int kXtyChunks = 32;     // row chunks of X0^T T (partial sums, reduced in order)
+constexpr int kFroBlocks = 64;     // blocks per matrix of ||X0||_F^2 (partial sums, reduced in order)
+
 struct SketchWS {
-    float *rowsum, *colsum, *scale, *T, *Y, *acc, *fro;
+    float *rowsum, *colsum, *scale, *T, *Y, *Ypart, *acc, *fro, *fropart;
     int *nonfinite, *done, *status, *fin;
     template <class C>
     void carve(C &cv, long long B, long long m, long long n, long long s) {
@@ -31,6 +34,8 @@ struct SketchWS {
         scale = cv.template take<float>(B);
         T = cv.template take<float>(B * m * s);
         Y = cv.template take<float>(B * n * s);
+        Ypart = cv.template take<float>(B * kXtyChunks * n * s);
+        fropart = cv.template take<float>(B * kFroBlocks * 2);
         acc = cv.template take<float>(B * 4);
         fro = cv.template take<float>(B);
         nonfinite = cv.template take<int>(B);
@@ -63,23 +68,37 @@ __global__ void xy_kernel(const float *A, const float *scale, const float *Y, in
     }
 }
 
-// out[b][k][p] = (1/scale_b) sum_i A[b][i][k] T[b][i][p]     (X0^T T, one thread per (b, k))
-__global__ void xty_kernel(const float *A, const float *scale, const float *T, int m, int n, int s, float *out) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+// part[b][r][k][p] = (1/scale_b) sum over rows i of chunk r of A[b][i][k] T[b][i][p]
+// (X0^T T split over kXtyChunks row chunks; one thread per (b, r, k), coalesced over k)
+__global__ void xty_part_kernel(const float *A, const float *scale, const float *T, int m, int n, int s,
+                                float *part) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y, r = blockIdx.z;
     if (k >= n) return;
+    const int rows = (m + kXtyChunks - 1) / kXtyChunks;
+    const int i0 = r * rows, i1 = min(m, i0 + rows);
     const float *a = A + (long long)b * m * n;
     const float *t = T + (long long)b * m * s;
     const float sc = scale[b] > 0.f ? 1.f / scale[b] : 0.f;
     float acc[8];
 #pragma unroll
     for (int p = 0; p < 8; ++p) acc[p] = 0.f;
-    for (int i = 0; i < m; ++i) {
+    for (int i = i0; i < i1; ++i) {
         const float x = a[(long long)i * n + k] * sc;
 #pragma unroll
         for (int p = 0; p < 8; ++p) if (p < s) acc[p] += x * t[(long long)i * s + p];
     }
+    float *o = part + (((long long)b * kXtyChunks + r) * n + k) * s;
 #pragma unroll
-    for (int p = 0; p < 8; ++p) if (p < s) out[(long long)b * n * s + (long long)k * s + p] = acc[p];
+    for (int p = 0; p < 8; ++p) if (p < s) o[p] = acc[p];
+}
+
+// out[b][k][p] = sum_r part[b][r][k][p], in chunk order
+__global__ void xty_reduce_kernel(const float *part, int n, int s, float *out) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (idx >= (long long)n * s) return;
+    float v = 0.f;
+    for (int r = 0; r < kXtyChunks; ++r) v += part[((long long)b * kXtyChunks + r) * n * s + idx];
+    out[(long long)b * n * s + idx] = v;
 }
 
 // acc[b][j] += sum z .* y  (Hutchinson term for power j)
@@ -99,23 +118,26 @@ __global__ void zdot_kernel(const float *Z, const float *Y, int n, int s, int j,
     }
 }
 
-__global__ void fro_kernel(const float *A, const float *scale, long long mn, float *fro) {
-    __shared__ double red[32];
-    const int b = blockIdx.x;
+// ||X0||_F^2 per matrix: kFroBlocks compensated partial sums (hi, lo), reduced in order
+__global__ void fro_part_kernel(const float *A, const float *scale, long long mn, float *part) {
+    __shared__ float red[64];
+    const int b = blockIdx.y, blk = blockIdx.x;
     const float sc = scale[b] > 0.f ? 1.f / scale[b] : 0.f;
-    double v = 0.0;
-    for (long long i = threadIdx.x; i < mn; i += blockDim.x) {
-        const double x = (double)A[(long long)b * mn + i] * sc;
-        v += x * x;
+    ff v = ff_zero();
+    for (long long i = (long long)blk * blockDim.x + threadIdx.x; i < mn; i += (long long)kFroBlocks * blockDim.x) {
+        const float x = A[(long long)b * mn + i] * sc;
+        v = ff_fma(v, x, x);
     }
-    v = warp_sum(v);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        fro[b] = (float)t;
-    }
+    const float t = block_sum_ff(v, red);
+    if (threadIdx.x == 0) { part[((long long)b * kFroBlocks + blk) * 2] = t; part[((long long)b * kFroBlocks + blk) * 2 + 1] = 0.f; }
+}
+
+__global__ void fro_reduce_kernel(const float *part, int B, float *fro) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    ff v = ff_zero();
+    for (int k = 0; k < kFroBlocks; ++k) v = ff_add(v, ff{part[((long long)b * kFroBlocks + k) * 2], 0.f});
+    fro[b] = __fadd_rn(v.hi, v.lo);
 }
 
 __global__ void features_kernel(const float *acc, const float *fro, int B, int m, int n, int s, float *F) {
@@ -260,15 +282,17 @@ extern "C" int psvd_sketch_features(const float *A, const float *Z, int64_t s, f
     PSVD_TRY(cudaMemsetAsync(w.nonfinite, 0, sizeof(int) * batch, st));
     PSVD_TRY(l1_norms(A, B, M, Nn, w.rowsum, w.colsum, w.nonfinite, st));
     norm_finalize_kernel<<<B, 256, 0, st>>>(w.rowsum, w.colsum, w.nonfinite, M, Nn, w.scale, w.done, w.status, w.fin);
-    fro_kernel<<<B, 256, 0, st>>>(A, w.scale, (long long)m * n, w.fro);
-    count_launch(2);
+    fro_part_kernel<<<dim3(kFroBlocks, B), 256, 0, st>>>(A, w.scale, (long long)m * n, w.fropart);
+    fro_reduce_kernel<<<(B + 127) / 128, 128, 0, st>>>(w.fropart, B, w.fro);
+    count_launch(3);
     // Y_{j+1} = X0^T (X0 Y_j), Y_0 = Z; f_j = <Z, Y_{j+1}> / (n s)
     const float *Y = Z;
     for (int j = 0; j < 4; ++j) {
         xy_kernel<<<dim3((M * 32 + 255) / 256, B), 256, 0, st>>>(A, w.scale, Y, M, Nn, S, w.T);
-        xty_kernel<<<dim3((Nn + 127) / 128, B), 128, 0, st>>>(A, w.scale, w.T, M, Nn, S, w.Y);
+        xty_part_kernel<<<dim3((Nn + 127) / 128, B, kXtyChunks), 128, 0, st>>>(A, w.scale, w.T, M, Nn, S, w.Ypart);
+        xty_reduce_kernel<<<dim3((unsigned)(((long long)Nn * S + 255) / 256), B), 256, 0, st>>>(w.Ypart, Nn, S, w.Y);
         zdot_kernel<<<B, 256, 0, st>>>(Z, w.Y, Nn, S, j, w.acc);
-        count_launch(3);
+        count_launch(4);
         Y = w.Y;
     }
     features_kernel<<<(B + 127) / 128, 128, 0, st>>>(w.acc, w.fro, B, M, Nn, S, F);
