@@ -1,0 +1,119 @@
+"""The workload configurations at their full sizes, through the C ABI, in the launch shape
+the benchmark uses (one call per batch).
+
+Sizes the FP64 oracle cannot finish in seconds are checked through properties that hold
+at any size: constructed inputs against their known spectrum with Weyl's bound for the
+input rounding, reconstruction and orthogonality computed in FP64 on the device, and, for
+the Marchenko-Pastur batch, sampled matrices against LAPACK's FP64 singular values (the
+oracle's own SVD is pinned to LAPACK in tests/test_oracle_forward.py).  Where the oracle is
+fast enough (the 512 x 512 backward), sampled matrices are compared with it directly."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import psvd_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+def _props(A, U, S, VT):
+    """FP64 reconstruction and orthogonality errors per matrix, on the device."""
+    out = []
+    for b in range(A.shape[0]):
+        a, u, s, vt = A[b].double(), U[b].double(), S[b].double(), VT[b].double()
+        n = s.shape[0]
+        eye = torch.eye(n, dtype=torch.float64, device=a.device)
+        rec = float(torch.linalg.matrix_norm(a - (u * s) @ vt) / torch.linalg.matrix_norm(a))
+        ou = float(torch.linalg.matrix_norm(u.T @ u - eye) / n ** 0.5)
+        ov = float(torch.linalg.matrix_norm(vt @ vt.T - eye) / n ** 0.5)
+        out.append((rec, ou, ov))
+    return out
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_config_marchenko_pastur_batch(precision):
+    # 8 x (4096 x 1024), iid N(0, 1/1024): plain FP32 path and mixed path
+    import paper_2609_32505_gb300 as P
+    a = np.stack([W.marchenko_pastur(100 + i, 4096, 1024) for i in range(8)]).astype(np.float32)
+    A = torch.from_numpy(a).cuda()
+    U, S, VT, info = P.svd_fwd(A, P.make_opts(precision=precision), return_info=True)
+    torch.cuda.synchronize()
+    assert all(i["status"] == 0 for i in info)
+    for rec, ou, ov in _props(A, U, S, VT):
+        assert rec <= 1e-5 and ou <= 1e-4 and ov <= 1e-4, (rec, ou, ov)
+    s = S.cpu().double().numpy()
+    for b in (0, 5):
+        s_ref = np.linalg.svd(a[b].astype(np.float64), compute_uv=False)
+        assert np.abs(s[b] - s_ref).max() <= 1e-5 * s_ref[0]
+
+
+def test_config_weight_shaped_bf16_inputs():
+    # 4 x (4096 x 14336) weight-shaped matrices rounded to BF16, processed as their
+    # 14336 x 4096 transposes; sigma_i = i^-0.7 (kappa ~ 338) and the kappa = 1e4 variant
+    # (exponent 1.107), mixed-precision forward only
+    import paper_2609_32505_gb300 as P
+    m, n = 14336, 4096
+    rng = W.rng_for(200)
+    q1 = torch.from_numpy(W.orthonormal(rng, m, n)).cuda()
+    q2 = torch.from_numpy(W.orthonormal(rng, n, n)).cuda()
+    i = np.arange(1, n + 1, dtype=np.float64)
+    spectra = [i ** -0.7, i ** -1.107, 2.0 * i ** -0.7, 0.5 * i ** -1.107]
+    A64 = torch.stack([(q1 * torch.from_numpy(s).cuda()[None, :]) @ q2.T for s in spectra])
+    A = A64.to(torch.bfloat16).float()             # inputs rounded to BF16
+    weyl = [float(torch.linalg.matrix_norm(A[b].double() - A64[b])) for b in range(4)]   # >= ||.||_2
+    del A64
+    U, S, VT, info = P.svd_fwd(A, P.make_opts(precision=P.PREC_MIXED), return_info=True)
+    torch.cuda.synchronize()
+    assert all(x["status"] == 0 for x in info)
+    s = S.cpu().double().numpy()
+    for b in range(4):
+        assert np.abs(s[b] - spectra[b]).max() <= 1e-5 * spectra[b][0] + weyl[b]
+    for rec, ou, ov in _props(A, U, S, VT):
+        assert rec <= 1e-5 and ou <= 1e-4 and ov <= 1e-4, (rec, ou, ov)
+
+
+def test_config_clustered_backward_batch():
+    # 64 x (512 x 512) with 128 clusters of multiplicity 4; loss <W_U, U> + <w, sigma> +
+    # <W_V, V>: the Algorithm 4 gradient on the GPU factors against the FP64 oracle's
+    # Algorithm 4 on the same factors (sampled), eps = 1e-8
+    import paper_2609_32505_gb300 as P
+    B, n = 64, 512
+    mats, specs = zip(*[W.clustered_square(300 + b, n) for b in range(B)])
+    a = np.stack(mats).astype(np.float32)
+    A = torch.from_numpy(a).cuda()
+    U, S, VT = P.svd_fwd(A, P.make_opts())
+    w = [W.loss_weights(300 + b, n, n) for b in range(B)]
+    GU = torch.from_numpy(np.stack([x[0] for x in w]).astype(np.float32)).cuda()
+    GS = torch.from_numpy(np.stack([x[1] for x in w]).astype(np.float32)).cuda()
+    GVT = torch.from_numpy(np.stack([x[2].T for x in w]).astype(np.float32)).cuda()
+    dA = P.svd_bwd(A, U, S, VT, GU, GS, GVT, eps=1e-8, kreg_mode=0)
+    torch.cuda.synchronize()
+    s = S.cpu().double().numpy()
+    for b in range(B):
+        assert np.abs(s[b] - specs[b]).max() <= 1e-5 * specs[b][0] + 1e-6
+    u, vt, g = U.cpu().double().numpy(), VT.cpu().double().numpy(), dA.cpu().double().numpy()
+    for b in (0, 17, 63):
+        ref = O.svd_bwd(a[b].astype(np.float64), u[b], s[b], vt[b], w[b][0], w[b][1], w[b][2].T, eps=1e-8,
+                        kreg_mode=0)
+        assert np.linalg.norm(g[b] - ref) <= 1e-3 * np.linalg.norm(ref)
+
+
+def test_config_learned_schedule_families():
+    # three spectrum families at 1024 x 1024 (held-out seeds): the trained lower bound
+    # against the conservative schedule, at the same tolerance
+    import paper_2609_32505_gb300 as P
+    from paper_2609_32505_gb300 import train_schedule as T
+    params, margin, nprobe = T.load()
+    A = T.family_batch(list(range(400, 432)), 1024, torch.device("cuda"))
+    Z = P.rademacher_probes(A.shape[0], 1024, nprobe, seed=11)
+    lb = P.predict_lower_bound(A, params, margin, z=Z)
+    _, _, info_c = P.polar(A, P.make_opts(), want_h=False, return_info=True)
+    _, _, info_l = P.polar(A, P.make_opts(schedule=P.SCHED_LEARNED, lower_bound=lb), want_h=False, return_info=True)
+    # rank-64 + noise matrices can be too ill-conditioned for the 50-step cap either way
+    ok = [b for b in range(len(info_c)) if info_c[b]["status"] == 0]
+    assert len(ok) >= len(info_c) // 2
+    assert all(info_l[b]["status"] == 0 and info_l[b]["ortho_resid"] <= 1e-5 for b in ok)
+    steps_c = np.mean([info_c[b]["iters"] for b in ok])
+    steps_l = np.mean([info_l[b]["iters"] for b in ok])
+    assert steps_l < steps_c, (steps_l, steps_c)
