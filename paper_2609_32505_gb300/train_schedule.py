@@ -1,6 +1,7 @@
 """Trains the lower-bound network of the learned polynomial schedule on the GPU.
 
     python -m paper_2609_32505_gb300.train_schedule [--out paper_2609_32505_gb300/schedule_mlp.npz]
+    python -m paper_2609_32505_gb300.train_schedule --evaluate 2048      (held-out comparison)
 
 Training data are spectra the method itself produces: seeded matrices from the three
 families of the learned-schedule study (geometric spectra with kappa in [1e1, 1e6], power
@@ -79,7 +80,12 @@ def main(argv=None):
     ap.add_argument("--sizes", default="256:768,512:512,1024:256,2048:96,4096:32")
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--quantile", type=float, default=0.95)
+    ap.add_argument("--evaluate", type=int, default=0, help="evaluate the stored network on this many matrices")
     a = ap.parse_args(argv)
+    if a.evaluate:
+        P.lib()
+        evaluate(a.evaluate, path=a.out)
+        return
     dev = torch.device("cuda")
     P.lib()
     F, Y = [], []
@@ -105,6 +111,49 @@ def main(argv=None):
              heldout_median_abs=np.float32(resid.median().item()), count=np.int32(F.shape[0]))
     print(f"trained on {F.shape[0] - nh}, held out {nh}: loss {curve[0]:.3f} -> {curve[-1]:.4f}, "
           f"held-out median |log error| {resid.median().item():.3f}, margin {margin:.3f} -> {a.out}")
+
+
+def evaluate(count: int, n: int = 1024, chunk: int = 64, path: str = DEFAULT_OUT):
+    """Held-out matrices of the three families (seeds 400, 401, ...): steps and device time of
+    the conservative and the learned schedule (bound prediction included), same tolerance."""
+    dev = torch.device("cuda")
+    params, margin, nprobe = load(path, dev)
+    tot = {"cons_ms": 0.0, "learn_ms": 0.0, "pred_ms": 0.0}
+    steps_c, steps_l, n_ok, n_fb, n_fail = [], [], 0, 0, 0
+
+    def timed(f):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        r = f()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    for c in range(0, count, chunk):
+        seeds = list(range(400 + c, 400 + min(count, c + chunk)))
+        A = family_batch(seeds, n, dev)
+        Z = P.rademacher_probes(len(seeds), n, nprobe, seed=400 + c, device=dev)
+        lb, t = timed(lambda: P.predict_lower_bound(A, params, margin, z=Z))
+        tot["pred_ms"] += t
+        (_, _, ic), t = timed(lambda: P.polar(A, P.make_opts(), want_h=False, return_info=True))
+        tot["cons_ms"] += t
+        o = P.make_opts(schedule=P.SCHED_LEARNED, lower_bound=lb)
+        (_, _, il), t = timed(lambda: P.polar(A, o, want_h=False, return_info=True))
+        tot["learn_ms"] += t
+        for a, b in zip(ic, il):
+            if a["status"] != 0:
+                n_fail += 1
+                continue
+            n_ok += 1
+            n_fb += b["sched_fallback"]
+            steps_c.append(a["iters"])
+            steps_l.append(b["iters"])
+        del A
+    print(f"{count} matrices of {n} x {n}: {n_ok} converged under the conservative schedule ({n_fail} hit the "
+          f"cap); mean steps conservative {np.mean(steps_c):.2f}, learned {np.mean(steps_l):.2f} "
+          f"({n_fb} conservative reruns); device time conservative {tot['cons_ms']:.1f} ms, learned "
+          f"{tot['learn_ms']:.1f} ms + bound prediction {tot['pred_ms']:.1f} ms")
 
 
 def load(path: str = DEFAULT_OUT, device="cuda"):
