@@ -91,11 +91,8 @@ class ClockSampler:
 
 
 def _dist():
-    import torch.distributed as dist
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    if ws > 1 and not dist.is_initialized():
-        dist.init_process_group("nccl")
-    return (dist.get_rank() if ws > 1 else 0), ws
+    from paper_2609_32505_gb300 import replicas
+    return replicas.init("nccl")
 
 
 def reference_arm(args):
@@ -254,9 +251,8 @@ def main():
                     launches_plain += P.kernel_launches() - c0
     ms_mixed, ms_plain = float(np.mean(t_mixed)), float(np.mean(t_plain))
     if ws > 1:
-        t = torch.tensor([ms_mixed, ms_plain], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_mixed, ms_plain = t.tolist()
+        from paper_2609_32505_gb300 import replicas
+        ms_mixed, ms_plain = replicas.max_over_ranks([ms_mixed, ms_plain], device=dev)
 
     # accuracy of this very run (factors of the timed input against its known spectrum)
     info_m = P.info_dict(mixed[5])[0]
