@@ -33,6 +33,9 @@ N = 4096
 KAPPA = 10.0
 EPS = 1e-8
 METRIC = "SVD fwd+bwd ms at 4096^2, f32-accurate: mixed vs plain path; % tensor-core peak"
+# dram__bytes_read.sum + dram__bytes_write.sum of one sytrd_kernel launch at n = 4096 (ncu
+# capture listed in profiles/sytrd_4096.md; valid while the kernel is unchanged)
+TRD_DRAM_BYTES = 99786240 + 5610412544
 
 
 def _peaks():
@@ -306,7 +309,7 @@ def main():
     trd = cls(prof_m, 4)
     trd_gbs = trd["work"] / (trd["ms"] * 1e-3) / 1e9 if trd["ms"] > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": trd_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": trd_gbs / hbm_peak,
-                "traffic": None,
+                "traffic": TRD_DRAM_BYTES if N == 4096 else None,
                 "kernel": "sytrd_kernel (Householder tridiagonalization of H, eigensolver stage 1; one launch)",
                 "algorithmic_bytes": trd["work"], "ms": trd["ms"], "share_of_step": trd["ms"] / ms_mixed,
                 "peak_src": f"{peak_src} HBM copy {hbm_peak:.0f} GB/s",

@@ -778,18 +778,24 @@ __global__ void larft_kernel(const float *Gm, const float *tau, int n, int nblk,
     for (int p = threadIdx.x; p < kWY * kWY; p += blockDim.x) out[p] = T[p];
 }
 
-// S2 = S T^T (n x nb), split into TF32 hi/lo.
-__global__ void s_times_tt_kernel(const float *S, const float *Tm, int n, int nblk, int blk, int nb, float *S2hi,
-                                  float *S2lo) {
+// S2 = S T^T (n x nb), split into TF32 hi/lo; S is the sum of `ks` K-split slices of
+// B x n x kWY each, added in slice order.
+__global__ void s_times_tt_kernel(const float *S, int ks, int B, const float *Tm, int n, int nblk, int blk, int nb,
+                                  float *S2hi, float *S2lo) {
     const int b = blockIdx.y;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // over n * kWY
     if (idx >= (long long)n * kWY) return;
     const int i = (int)(idx / kWY), j = (int)(idx % kWY);
     const float *Tb = Tm + ((long long)b * nblk + blk) * kWY * kWY;
+    const long long slice = (long long)B * n * kWY;
     const float *Si = S + (long long)b * n * kWY + (long long)i * kWY;
     float acc = 0.f;
     if (j < nb)
-        for (int l = j; l < nb; ++l) acc += Si[l] * Tb[j * kWY + l];
+        for (int l = j; l < nb; ++l) {
+            float sv = Si[l];
+            for (int c = 1; c < ks; ++c) sv += Si[c * slice + l];
+            acc += sv * Tb[j * kWY + l];
+        }
     float h, lo;
     split_tf32(acc, h, lo);
     S2hi[(long long)b * n * kWY + idx] = h;
@@ -966,7 +972,8 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
             const int nb = std::min(kWY, n - 2 - k0);
             const int r0 = ((k0 + 1) / 32) * 32;
             const int Lr = n - r0;
-            // S = V^T[:, r0:] Y[r0:, blk]   (n x nb)
+            int ks = 1;
+            // S = V^T[:, r0:] Y[r0:, blk]   (n x nb), as ks partial sums over K
             {
                 MatView ahi = view_of(w.VThi + r0, n, Lr, ldn, (long long)n * ldn, B);
                 MatView alo = view_of(w.VTlo + r0, n, Lr, ldn, (long long)n * ldn, B);
@@ -975,12 +982,17 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
                 GemmShape s;
                 memset(&s, 0, sizeof(s));
                 s.M = n; s.N = nb; s.K = Lr; s.prec_uniform = PREC_TF32X3; s.err = w.err;
+                // N = nb <= 128 leaves ceil(n / 128) tiles per matrix: split K so that about
+                // one wave of CTAs runs, at least 4 k-blocks per range
+                const int tiles = ((n + kBM - 1) / kBM) * B;
+                s.ksplit = std::max(1, std::min(std::min(kBtSplit, (num_sms() + tiles - 1) / tiles), Lr / 128));
+                ks = s.ksplit;
                 EpiStore e = epi_store_plain(w.S, kWY, (long long)n * kWY, n, nb);
                 PSVD_TRY(launch_gemm(nullptr, nullptr, &ahi, &alo, &bhi, &blo, s, B, e, st));
             }
             {
                 dim3 g((unsigned)(((long long)n * kWY + 255) / 256), B);
-                s_times_tt_kernel<<<g, 256, 0, st>>>(w.S, w.Tm, n, w.nblk, blk, nb, w.S2hi, w.S2lo);
+                s_times_tt_kernel<<<g, 256, 0, st>>>(w.S, ks, B, w.Tm, n, w.nblk, blk, nb, w.S2hi, w.S2lo);
                 PSVD_TRY(cudaGetLastError());
                 count_launch(1);
             }

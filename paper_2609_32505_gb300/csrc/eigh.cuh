@@ -7,6 +7,7 @@
 namespace psvd {
 
 constexpr int kWY = 128;   // reflectors per compact-WY block in the back-transform
+constexpr int kBtSplit = 8; // largest K split of the back-transform's V^T Y products
 
 struct EighWS {
     int B = 0, n = 0, nblk = 0, chunk = 0, nrp = 0;   // nrp: rows of Vh, padded to kWY
@@ -53,7 +54,7 @@ struct EighWS {
         Ylo = cv.template take<float>(B64 * nn);
         VThi = cv.template take<float>(B64 * nn);
         VTlo = cv.template take<float>(B64 * nn);
-        S = cv.template take<float>(B64 * n * kWY);
+        S = cv.template take<float>(kBtSplit * B64 * n * kWY);
         S2hi = cv.template take<float>(B64 * n * kWY);
         S2lo = cv.template take<float>(B64 * n * kWY);
         Tm = cv.template take<float>(B64 * (nblk > 0 ? nblk : 1) * kWY * kWY);

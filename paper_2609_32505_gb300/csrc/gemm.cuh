@@ -56,6 +56,8 @@ struct GemmShape {
     int bn;                 // 128 or 256
     int batch;
     int sym;                // 1: only tiles that reach the upper triangle (col >= row); requires A == B
+    int ksplit;             // > 1: every tile repeated over ksplit disjoint k-block ranges; the
+                            // epilogue of range kc gets batch index b + kc * batch (partial sums)
     int prec_uniform;       // used when prec == nullptr
     const int *prec;        // [batch] per-matrix precision, or nullptr
     const int *skip;        // [batch] nonzero = matrix finished, its tiles are skipped (or nullptr)
@@ -92,6 +94,25 @@ PSVD_DEV int kblocks(const GemmShape &s, int prec) {
     return (s.K + kstep - 1) / kstep;
 }
 
+// One work item of the persistent tile list: matrix b, k range kc (of ksplit), tile (ti, tj),
+// k-blocks [kb0, kb0 + nkb).
+struct TileJob { int b, kc, ti, tj, kb0, nkb, prec; };
+PSVD_DEV TileJob tile_job(const GemmShape &s, int t, int tpm) {
+    TileJob j;
+    const int ks = s.ksplit > 1 ? s.ksplit : 1;
+    const int per = tpm * ks;
+    j.b = t / per;
+    const int rem = t % per;
+    j.kc = rem / tpm;
+    tile_coords(s, rem % tpm, j.ti, j.tj);
+    j.prec = s.prec ? s.prec[j.b] : s.prec_uniform;
+    const int all = kblocks(s, j.prec);
+    const int each = (all + ks - 1) / ks;
+    j.kb0 = j.kc * each;
+    j.nkb = max(0, min(all, j.kb0 + each) - j.kb0);
+    return j;
+}
+
 template <class Epi>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 gemm_tn_kernel(const __grid_constant__ GemmMaps maps, const GemmShape shp, Epi epi) {
@@ -121,8 +142,8 @@ gemm_tn_kernel(const __grid_constant__ GemmMaps maps, const GemmShape shp, Epi e
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int per = tiles_per_matrix(shp);
-    const int total = per * shp.batch;
+    const int tpm = tiles_per_matrix(shp);
+    const int total = tpm * (shp.ksplit > 1 ? shp.ksplit : 1) * shp.batch;
     const int bn = shp.bn;
     const uint32_t unit_bytes = (uint32_t)(kUnitA + bn * 128);
 
@@ -131,13 +152,10 @@ gemm_tn_kernel(const __grid_constant__ GemmMaps maps, const GemmShape shp, Epi e
         if (lane == 0) {
             uint32_t u = 0;
             for (int t = blockIdx.x; t < total && !s_abort; t += gridDim.x) {
-                const int b = t / per;
+                const TileJob jb = tile_job(shp, t, tpm);
+                const int b = jb.b, prec = jb.prec, nkb = jb.nkb;
                 if (shp.skip && shp.skip[b]) continue;
-                int ti, tj;
-                tile_coords(shp, t % per, ti, tj);
-                const int prec = shp.prec ? shp.prec[b] : shp.prec_uniform;
-                const int nkb = kblocks(shp, prec);
-                const int row_a = ti * kBM, row_b = tj * bn;
+                const int row_a = jb.ti * kBM, row_b = jb.tj * bn;
                 for (int kb = 0; kb < nkb; ++kb) {
                     const int nu = prec == PREC_TF32X3 ? 2 : 1;
                     for (int h = 0; h < nu; ++h, ++u) {
@@ -147,9 +165,10 @@ gemm_tn_kernel(const __grid_constant__ GemmMaps maps, const GemmShape shp, Epi e
                         mbar_arrive_expect_tx(&full[s], unit_bytes);
                         const CUtensorMap *ma, *mb;
                         int k0;
-                        if (prec == PREC_BF16) { ma = &maps.a_bf16; mb = &maps.b_bf16; k0 = kb * 64; }
-                        else if (prec == PREC_TF32) { ma = &maps.a_hi; mb = &maps.b_hi; k0 = kb * 32; }
-                        else { ma = h ? &maps.a_lo : &maps.a_hi; mb = h ? &maps.b_lo : &maps.b_hi; k0 = kb * 32; }
+                        const int kg = jb.kb0 + kb;
+                        if (prec == PREC_BF16) { ma = &maps.a_bf16; mb = &maps.b_bf16; k0 = kg * 64; }
+                        else if (prec == PREC_TF32) { ma = &maps.a_hi; mb = &maps.b_hi; k0 = kg * 32; }
+                        else { ma = h ? &maps.a_lo : &maps.a_hi; mb = h ? &maps.b_lo : &maps.b_hi; k0 = kg * 32; }
                         tma_load_3d(st, ma, &full[s], k0, row_a, b);
                         tma_load_3d(st + kUnitA, mb, &full[s], k0, row_b, b);
                     }
@@ -165,10 +184,9 @@ gemm_tn_kernel(const __grid_constant__ GemmMaps maps, const GemmShape shp, Epi e
             uint32_t u = 0, q = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-                const int b = t / per;
+                const TileJob jb = tile_job(shp, t, tpm);
+                const int b = jb.b, prec = jb.prec, nkb = jb.nkb;
                 if (shp.skip && shp.skip[b]) continue;
-                const int prec = shp.prec ? shp.prec[b] : shp.prec_uniform;
-                const int nkb = kblocks(shp, prec);
                 const bool x3 = prec == PREC_TF32X3;
                 for (int kb = 0; kb < nkb && ok; ++kb) {
                     const bool phase_start = x3 || kb == 0;
@@ -230,12 +248,10 @@ gemm_tn_kernel(const __grid_constant__ GemmMaps maps, const GemmShape shp, Epi e
         const uint32_t lane_base = uint32_t(quad * 32) << 16;
         uint32_t q = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x) {
-            const int b = t / per;
+            const TileJob jb = tile_job(shp, t, tpm);
+            const int b = jb.b, prec = jb.prec, nkb = jb.nkb, ti = jb.ti, tj = jb.tj;
             if (shp.skip && shp.skip[b]) continue;
-            int ti, tj;
-            tile_coords(shp, t % per, ti, tj);
-            const int prec = shp.prec ? shp.prec[b] : shp.prec_uniform;
-            const int nkb = kblocks(shp, prec);
+            const int be = b + jb.kc * shp.batch;     // epilogue's batch index (partial-sum slice)
             const int nph = nkb == 0 ? 0 : (prec == PREC_TF32X3 ? nkb : 1);
             float acc[128];
 #pragma unroll
@@ -273,10 +289,10 @@ gemm_tn_kernel(const __grid_constant__ GemmMaps maps, const GemmShape shp, Epi e
                     float v[16];
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] = acc[c + i];
-                    epi.chunk(ea, b, r, cbase + c, ti, tj, v);
+                    epi.chunk(ea, be, r, cbase + c, ti, tj, v);
                 }
             }
-            epi.finish(ea, b, ti, tj);
+            epi.finish(ea, be, ti, tj);
         }
         tc_fence_before();
     }
@@ -352,7 +368,7 @@ cudaError_t launch_gemm(const MatView *a16, const MatView *b16, const MatView *a
     shp.tiles_n = (shp.N + shp.bn - 1) / shp.bn;
     shp.batch = batch;
     if (shp.tiles_m == 0 || shp.tiles_n == 0 || batch == 0) return cudaSuccess;
-    const long long total = (long long)host_tiles_per_matrix(shp) * batch;
+    const long long total = (long long)host_tiles_per_matrix(shp) * (shp.ksplit > 1 ? shp.ksplit : 1) * batch;
     const int grid = (int)std::min<long long>(total, num_sms());
     const bool prof = prof_on();
     if (prof) prof_begin(st);
