@@ -189,6 +189,27 @@ PSVD_DEV void group_barrier(unsigned *ctr, unsigned target, unsigned *err) {
     __syncthreads();
 }
 
+// Counter barrier over co-resident CTAs with release/acquire operations instead of full
+// fences: thread 0 of each CTA adds 1 with release semantics (its CTA's writes, ordered
+// before it by the CTA barrier, become visible with it) and polls the counter with
+// acquire loads until it reaches `target`; bounded, stops early on a raised error word.
+template <int kSleepNs>
+PSVD_DEV void counter_barrier(unsigned *ctr, unsigned target, unsigned *err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
+        for (uint32_t i = 0;; ++i) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+            if (v >= target) break;
+            if (i > kBarrierSpin) { atomicOr(err, DEV_ERR_TIMEOUT); break; }
+            if ((i & 63) == 63 && *(volatile unsigned *)err) break;
+            if (kSleepNs > 0) __nanosleep(kSleepNs);
+        }
+    }
+    __syncthreads();
+}
+
 // Flag barrier over `g` co-resident CTAs: CTA c publishes arrive[c] = gen; CTA 0 polls all
 // arrival flags in parallel and publishes release = gen, which every other CTA polls.
 // Every wait is bounded and stops at once when the error word is raised elsewhere.

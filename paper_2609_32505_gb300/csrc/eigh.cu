@@ -19,12 +19,13 @@
 
 namespace psvd {
 
-// Launch shape of the tridiagonalization (compile-time; measured on GB300 at n = 4096:
-// 512 threads and one CTA per SM beat 256 x 2; the release-flag barrier with short
-// sleeps between polls beat both every CTA polling every flag (30% slower) and polling
-// without sleeps (7% slower: the pollers contend for the flag's L2 line)).  The per-step row pass moves the trailing matrix
-// through L2 twice, so it is bound by SM-L2 bandwidth: use every SM once the matrix
-// has enough rows (one CTA per 24 rows).
+// Launch shape of the tridiagonalization (compile-time; measured on GB300 at n = 4096):
+// 512 threads and one CTA per SM beat 256 x 2; the grid barrier is an arrival counter
+// every CTA polls (release add, acquire loads): eigh 66.4 ms, against 67.3 with fenced
+// atomics, 76.5 with a release flag that one CTA sets after polling every arrival flag,
+// and 30% more when every CTA polls every flag.  The per-step row pass moves the trailing
+// matrix through L2 twice, so it is bound by SM-L2 bandwidth: use every SM once the
+// matrix has enough rows (one CTA per 24 rows).
 #ifndef PSVD_TRD_THREADS
 #define PSVD_TRD_THREADS 512
 #endif
@@ -35,7 +36,10 @@ namespace psvd {
 #define PSVD_TRD_ROWDIV 24
 #endif
 #ifndef PSVD_TRD_BARRIER
-#define PSVD_TRD_BARRIER 0      // 0: release flag, 1: every CTA polls every flag
+#define PSVD_TRD_BARRIER 3      // 0: release flag, 1: every CTA polls every flag, 2: arrival counter,
+#endif                          // 3: arrival counter with release/acquire operations
+#ifndef PSVD_TRD_SLEEP
+#define PSVD_TRD_SLEEP 40
 #endif
 constexpr int kTrdThreads = PSVD_TRD_THREADS;
 struct TrdParams {
@@ -184,6 +188,10 @@ __global__ void __launch_bounds__(kTrdThreads, PSVD_TRD_MINB) sytrd_kernel(TrdPa
     unsigned nbar = 0;
 #if PSVD_TRD_BARRIER == 1
 #define TRD_BARRIER() flag_barrier_all(arr, cig, P.g, ++nbar, P.err)
+#elif PSVD_TRD_BARRIER == 2
+#define TRD_BARRIER() group_barrier(rel, (unsigned)P.g * (++nbar), P.err)
+#elif PSVD_TRD_BARRIER == 3
+#define TRD_BARRIER() counter_barrier<PSVD_TRD_SLEEP>(rel, (unsigned)P.g * (++nbar), P.err)
 #else
 #define TRD_BARRIER() flag_barrier(arr, rel, cig, P.g, ++nbar, P.err)
 #endif
