@@ -787,27 +787,25 @@ __global__ void larft_kernel(const float *Gm, const float *tau, int n, int nblk,
 }
 
 // S2 = S T^T (n x nb), split into TF32 hi/lo; S is the sum of `ks` K-split slices of
-// B x n x kWY each, added in slice order.
+// B x n x kWY each, added in slice order.  One block of kWY threads per row of S.
 __global__ void s_times_tt_kernel(const float *S, int ks, int B, const float *Tm, int n, int nblk, int blk, int nb,
                                   float *S2hi, float *S2lo) {
-    const int b = blockIdx.y;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // over n * kWY
-    if (idx >= (long long)n * kWY) return;
-    const int i = (int)(idx / kWY), j = (int)(idx % kWY);
-    const float *Tb = Tm + ((long long)b * nblk + blk) * kWY * kWY;
+    __shared__ float srow[kWY];
+    const int i = blockIdx.x, b = blockIdx.y, j = threadIdx.x;
     const long long slice = (long long)B * n * kWY;
-    const float *Si = S + (long long)b * n * kWY + (long long)i * kWY;
+    const long long o = (long long)b * n * kWY + (long long)i * kWY + j;
+    float sv = S[o];
+    for (int c = 1; c < ks; ++c) sv += S[c * slice + o];
+    srow[j] = sv;
+    __syncthreads();
+    const float *Tb = Tm + ((long long)b * nblk + blk) * kWY * kWY + (long long)j * kWY;
     float acc = 0.f;
     if (j < nb)
-        for (int l = j; l < nb; ++l) {
-            float sv = Si[l];
-            for (int c = 1; c < ks; ++c) sv += Si[c * slice + l];
-            acc += sv * Tb[j * kWY + l];
-        }
+        for (int l = j; l < nb; ++l) acc += srow[l] * Tb[l];
     float h, lo;
     split_tf32(acc, h, lo);
-    S2hi[(long long)b * n * kWY + idx] = h;
-    S2lo[(long long)b * n * kWY + idx] = lo;
+    S2hi[o] = h;
+    S2lo[o] = lo;
 }
 
 // V^T[:, r0 + c] -= acc, kept split in hi/lo.
@@ -816,6 +814,17 @@ struct EpiSubSplit {
     float *hi, *lo;
     long long ld, bs;
     struct Acc {};
+    static constexpr bool kElem = true;
+    PSVD_DEV bool staged() const { return true; }
+    PSVD_DEV void elem(Acc &, int b, int r, int c, float v) const {
+        if (r >= rows || c >= cols) return;
+        const long long o = b * bs + (long long)r * ld + c;
+        const float x = (hi[o] + lo[o]) - v;
+        float h, l;
+        split_tf32(x, h, l);
+        hi[o] = h;
+        lo[o] = l;
+    }
     PSVD_DEV void begin(Acc &) const {}
     PSVD_DEV void chunk(Acc &, int b, int r, int c0, int, int, float (&v)[16]) const {
         if (r >= rows) return;
@@ -999,8 +1008,7 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
                 PSVD_TRY(launch_gemm(nullptr, nullptr, &ahi, &alo, &bhi, &blo, s, B, e, st));
             }
             {
-                dim3 g((unsigned)(((long long)n * kWY + 255) / 256), B);
-                s_times_tt_kernel<<<g, 256, 0, st>>>(w.S, ks, B, w.Tm, n, w.nblk, blk, nb, w.S2hi, w.S2lo);
+                s_times_tt_kernel<<<dim3(n, B), kWY, 0, st>>>(w.S, ks, B, w.Tm, n, w.nblk, blk, nb, w.S2hi, w.S2lo);
                 PSVD_TRY(cudaGetLastError());
                 count_launch(1);
             }

@@ -26,6 +26,7 @@
 #pragma once
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -40,7 +41,9 @@ constexpr int kUnitBytes = kUnitA + kUnitB;    // 48 KB
 constexpr int kStages = 4;
 constexpr int kEpiWarps = 8;
 constexpr int kGemmThreads = (kEpiWarps + 2) * 32;
-constexpr int kGemmSmem = kStages * kUnitBytes + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int kStageRow = 17;                  // staging row stride (floats): conflict-free
+constexpr int kStageBytes = kEpiWarps * 32 * kStageRow * 4;
+constexpr int kGemmSmem = kStages * kUnitBytes + 1024 /*align*/ + 256 /*barriers*/ + kStageBytes;
 constexpr int kAccCols = 256;                  // TMEM columns per accumulator
 constexpr uint32_t kTmemCols = 512;
 
@@ -113,6 +116,12 @@ PSVD_DEV TileJob tile_job(const GemmShape &s, int t, int tpm) {
     return j;
 }
 
+// Epilogues that define a per-element elem(acc, b, r, c, v) and a runtime staged() get
+// their values through a per-warp shared-memory transpose, so that each store instruction
+// of a warp covers two rows x 16 consecutive columns instead of 32 rows x 1 column.
+template <class E, class = void> struct EpiHasElem : std::false_type {};
+template <class E> struct EpiHasElem<E, std::void_t<decltype(E::kElem)>> : std::integral_constant<bool, E::kElem> {};
+
 template <class Epi>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 gemm_tn_kernel(const __grid_constant__ GemmMaps maps, const GemmShape shp, Epi epi) {
@@ -123,6 +132,7 @@ gemm_tn_kernel(const __grid_constant__ GemmMaps maps, const GemmShape shp, Epi e
     uint64_t *acc_full = empty + kStages;      // [2] accumulator phase complete (tcgen05.commit)
     uint64_t *acc_empty = acc_full + 2;        // [2] accumulator drained by the epilogue (8 warps)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+    float *stage = reinterpret_cast<float *>(smem + kStages * kUnitBytes + 256);
     __shared__ volatile int s_abort;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -283,13 +293,36 @@ gemm_tn_kernel(const __grid_constant__ GemmMaps maps, const GemmShape shp, Epi e
             const int cbase = tj * bn + half * ncols;
             typename Epi::Acc ea;
             epi.begin(ea);
+            bool staged = false;
+            if constexpr (EpiHasElem<Epi>::value) staged = epi.staged();
+            if (staged) {
+                if constexpr (EpiHasElem<Epi>::value) {
+                    float *sw = stage + warp * 32 * kStageRow;
+                    const int r0 = ti * kBM + quad * 32, rr0 = lane >> 4, cc = lane & 15;
 #pragma unroll
-            for (int c = 0; c < 128; c += 16) {
-                if (c < ncols) {
-                    float v[16];
+                    for (int c = 0; c < 128; c += 16) {
+                        if (c < ncols) {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] = acc[c + i];
-                    epi.chunk(ea, be, r, cbase + c, ti, tj, v);
+                            for (int i = 0; i < 16; ++i) sw[lane * kStageRow + i] = acc[c + i];
+                            __syncwarp();
+#pragma unroll 4
+                            for (int k = 0; k < 16; ++k) {
+                                const int rr = 2 * k + rr0;
+                                epi.elem(ea, be, r0 + rr, cbase + c + cc, sw[rr * kStageRow + cc]);
+                            }
+                            __syncwarp();
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 128; c += 16) {
+                    if (c < ncols) {
+                        float v[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v[i] = acc[c + i];
+                        epi.chunk(ea, be, r, cbase + c, ti, tj, v);
+                    }
                 }
             }
             epi.finish(ea, be, ti, tj);

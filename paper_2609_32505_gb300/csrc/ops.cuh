@@ -45,6 +45,21 @@ struct EpiStore {
     float *hi, *lo; long long ldh, bsh;                    // optional split store
     float *hi_t, *lo_t; long long ldht, bsht;              // optional split transposed store
     struct Acc {};
+    static constexpr bool kElem = true;
+    // staged (coalesced) element path when nothing is stored transposed
+    PSVD_DEV bool staged() const { return !out_t && !hi_t; }
+    PSVD_DEV void elem(Acc &, int b, int r, int c, float v) const {
+        if (r >= rows || c >= cols) return;
+        float x = alpha * v;
+        if (cin) x += beta * cin[b * bsc + (long long)r * ldc + c];
+        if (out) out[b * bs + (long long)r * ld + c] = x;
+        if (hi) {
+            float h, l;
+            split_tf32(x, h, l);
+            hi[b * bsh + (long long)r * ldh + c] = h;
+            if (lo) lo[b * bsh + (long long)r * ldh + c] = l;
+        }
+    }
     PSVD_DEV void begin(Acc &) const {}
     PSVD_DEV void chunk(Acc &, int b, int r, int c0, int, int, float (&v)[16]) const {
         if (r >= rows) return;
