@@ -36,6 +36,8 @@ METRIC = "SVD fwd+bwd ms at 4096^2, f32-accurate: mixed vs plain path; % tensor-
 # dram__bytes_read.sum + dram__bytes_write.sum of one sytrd_kernel launch at n = 4096 (ncu
 # capture listed in profiles/sytrd_4096.md; valid while the kernel is unchanged)
 TRD_DRAM_BYTES = 99786240 + 5610412544
+WORKLOAD = (f"SVD fwd+bwd of one {N}x{N} fp32 matrix A = Q1 diag(s) Q2^T, s_i = {KAPPA:g}^((n-i)/(n-1)), "
+            f"eps=1e-8, kreg Algorithm 4")
 
 
 def _peaks():
@@ -127,8 +129,8 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"SVD fwd+bwd {N}x{N} fp32 input, kappa={KAPPA:g} geometric spectrum, "
-                                   f"FP64 oracle timed at {n}x{n} and scaled by (4096/{n})^3"},
+            "config": {"workload": WORKLOAD,
+                       "reference": f"FP64 oracle timed at {n}x{n} on the host cores and scaled by (4096/{n})^3"},
             "cpu_baseline": {"value": ms, "unit": "ms", "cores": threads, "kind": "oracle",
                              "sample": f"one {n}x{n} fwd+bwd per step (median of {len(ts)}), x{scale:.0f}"},
             "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -354,8 +356,7 @@ def main():
         line = {"metric": METRIC, "value": ms_mixed / ws, "unit": "ms", "n_gpus": ws, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms_mixed, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": f"SVD fwd+bwd of one {N}x{N} fp32 matrix A = Q1 diag(s) Q2^T, "
-                                       f"s_i = {KAPPA:g}^((n-i)/(n-1)), eps=1e-8, kreg Algorithm 4",
+                "config": {"workload": WORKLOAD,
                            "path": "mixed: learned lower bound (sketch + MLP kernels) -> greedy cubics, TF32 steps "
                                    "-> split-TF32 polish, eigenbasis correction; plain: conservative CANS "
                                    "(delta=0.99), split-TF32 throughout",
