@@ -95,8 +95,10 @@ PSVD_DEV void load2_vec4(float *d1, const float *s1, float *d2, const float *s2,
         if (c < c1) { x4[c] = ra[u]; y4[c] = rb[u]; }
     }
     for (int c = c0 + threadIdx.x + 4 * blockDim.x; c < c1; c += blockDim.x) { x4[c] = a4[c]; y4[c] = b4[c]; }
-    __syncthreads();
-    for (int j = n + threadIdx.x; j < 4 * c1; j += blockDim.x) { d1[j] = 0.f; d2[j] = 0.f; }
+    if (n & 3) {                                   // uniform: a partial last chunk
+        __syncthreads();
+        for (int j = n + threadIdx.x; j < 4 * c1; j += blockDim.x) { d1[j] = 0.f; d2[j] = 0.f; }
+    }
 }
 
 // In place: x[j] -= vk w[j] + wk v[j] for j in [jstart, n) (row k+1 corrected by the
@@ -270,10 +272,9 @@ __global__ void __launch_bounds__(kTrdThreads, PSVD_TRD_MINB) sytrd_kernel(TrdPa
                 }
             }
             if (more) {
-                TRD_BARRIER();
+                TRD_BARRIER();                      // ends with a CTA barrier
                 float *t = bv; bv = bn; bn = t;     // v_{k+1} becomes current
                 tau_k = tau_n;
-                __syncthreads();
             }
         }
         TRD_BARRIER();
@@ -536,6 +537,18 @@ PSVD_DEV void iv_stream(double *ring, int nsteps, int na, Addr addr, Body body) 
 
 PSVD_DEV double iv_start(int i, int j) { return hash_unit((unsigned)i, (unsigned)j) + 0.0625; }
 
+// 1/a by the hardware's approximate reciprocal refined with two Newton-Raphson steps
+// (y <- y + y (1 - a y), each doubling the correct bits); |a| is kept >= tiny > 0 by the
+// pivot floor, far from the denormal and overflow ranges.
+PSVD_DEV double recip64(double a) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+    double e = fma(-a, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-a, y, 1.0);
+    return fma(y, e, y);
+}
+
 // Factor T - mu I = P L U (U with two superdiagonals, reciprocal pivots in u0).
 PSVD_DEV void iv_factor(const InvitParams &P, double *ring, const double *D, const double *E, int n, double mu,
                         double tiny, int t) {
@@ -554,13 +567,13 @@ PSVD_DEV void iv_factor(const InvitParams &P, double *ring, const double *D, con
                   const long long o = (long long)j * s + t;
                   if (fabs(a) >= fabs(c)) {
                       if (fabs(a) < tiny) a = a < 0 ? -tiny : tiny;
-                      const double ra = 1.0 / a;
+                      const double ra = recip64(a);
                       const double m = c * ra;
                       P.u0[o] = ra; P.u1[o] = bsup; P.u2[o] = 0.0; P.lm[o] = m;
                       a = dn - m * bsup;
                       bsup = en;
                   } else {
-                      const double rc = 1.0 / c;
+                      const double rc = recip64(c);
                       const double m = a * rc;
                       P.u0[o] = rc; P.u1[o] = dn; P.u2[o] = en; P.lm[o] = m;
                       word |= 1u << (j & 31);
@@ -570,7 +583,7 @@ PSVD_DEV void iv_factor(const InvitParams &P, double *ring, const double *D, con
                   if ((j & 31) == 31 || j == n - 2) { P.piv[(long long)(j >> 5) * s + t] = word; word = 0; }
               });
     if (fabs(a) < tiny) a = a < 0 ? -tiny : tiny;
-    P.u0[(long long)(n - 1) * s + t] = 1.0 / a;
+    P.u0[(long long)(n - 1) * s + t] = recip64(a);
 }
 
 // Forward part of one solve: x <- P-and-L applied to b, where b = scale * x, or the
