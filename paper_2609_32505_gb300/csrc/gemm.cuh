@@ -8,9 +8,11 @@
 //
 // Persistent kernel: one CTA per SM walks a static list of output tiles of
 // 128 x BN (BN = 256, or 128 when N <= 128), UMMA M = 128, N = BN, cta_group::1.
-// Shared memory holds a ring of kStages units of 48 KB, each one TMA'd k-block:
-// an A sub-tile (128 rows x 128 B) and a B sub-tile (BN rows x 128 B), both in the
-// canonical 128-byte-swizzled K-major layout:
+// 128-wide tiles cost about twice as much per flop as 256-wide ones on GB300 (measured:
+// BF16 at 8192^3, 559 against 1049 TFLOP/s), so they are used only where N <= 128.
+// Shared memory holds a 192 KB ring of units (4 x 48 KB at BN = 256, 6 x 32 KB at
+// BN = 128), each one TMA'd k-block: an A sub-tile (128 rows x 128 B) and a B sub-tile
+// (BN rows x 128 B), both in the canonical 128-byte-swizzled K-major layout:
 //   PREC_BF16   : 64 bf16 of K per unit, one unit per k-block
 //   PREC_TF32   : 32 fp32 of K per unit, one unit per k-block
 //   PREC_TF32X3 : 32 fp32 of K, two units per k-block (hi parts, lo parts);
@@ -38,12 +40,15 @@ constexpr int kBM = 128;
 constexpr int kUnitA = 16384;                  // 128 rows x 128 B
 constexpr int kUnitB = 32768;                  // up to 256 rows x 128 B
 constexpr int kUnitBytes = kUnitA + kUnitB;    // 48 KB
-constexpr int kStages = 4;
+constexpr int kStages = 4;                     // ring units at BN = 256
+constexpr int kRingBytes = kStages * kUnitBytes;
+constexpr int kMaxStages = kRingBytes / (kUnitA + 128 * 128);   // ring units at BN = 128 (6)
 constexpr int kEpiWarps = 8;
 constexpr int kGemmThreads = (kEpiWarps + 2) * 32;
 constexpr int kStageRow = 17;                  // staging row stride (floats): conflict-free
 constexpr int kStageBytes = kEpiWarps * 32 * kStageRow * 4;
-constexpr int kGemmSmem = kStages * kUnitBytes + 1024 /*align*/ + 256 /*barriers*/ + kStageBytes;
+constexpr int kGemmSmem = kRingBytes + 1024 /*align*/ + 256 /*barriers*/ + kStageBytes;
+static_assert((2 * kMaxStages + 4) * 8 + 4 <= 256, "barrier area");
 constexpr int kAccCols = 256;                  // TMEM columns per accumulator
 constexpr uint32_t kTmemCols = 512;
 
@@ -122,22 +127,97 @@ PSVD_DEV TileJob tile_job(const GemmShape &s, int t, int tpm) {
 template <class E, class = void> struct EpiHasElem : std::false_type {};
 template <class E> struct EpiHasElem<E, std::void_t<decltype(E::kElem)>> : std::integral_constant<bool, E::kElem> {};
 
+// Consumer side of the operand ring, as seen by the MMA issuer: shared-memory address of
+// unit 0, unit size, unit count, barriers, and the position of the next unit with the
+// parity of its current fill.
+struct MmaRing {
+    uint32_t base, unit_bytes, nst;
+    uint64_t *full, *empty;
+    unsigned *err;
+    uint32_t stage, phase;
+    PSVD_DEV uint32_t take() {                 // returns the stage, advances the position
+        const uint32_t s = stage;
+        if (++stage == nst) { stage = 0; phase ^= 1; }
+        return s;
+    }
+};
+
+// Descriptor of the k-th 32-byte K step inside a 128-byte swizzled row: the start address
+// field (bits 0-13, in 16-byte units) advances by 2; a unit ends below 228 KB, so the
+// field never carries.
+PSVD_DEV uint64_t sdesc_step(uint64_t d, int k) { return d + (uint64_t)(2 * k); }
+
+// One BF16 or TF32 tile: all its k-blocks accumulate into `tacc` (one phase).
+template <bool kTF32>
+PSVD_DEV bool mma_tile(MmaRing &r, int nkb, uint32_t tacc, uint32_t id) {
+    for (int kb = 0; kb < nkb; ++kb) {
+        const uint32_t par = r.phase;
+        const uint32_t s = r.take();
+        if (!mbar_wait(&r.full[s], par, r.err)) return false;
+        tc_fence_after();
+        const uint32_t a0 = r.base + s * r.unit_bytes;
+        const uint64_t ad = sdesc_k128(a0), bd = sdesc_k128(a0 + kUnitA);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t en = (kb > 0 || k > 0) ? 1u : 0u;
+            if constexpr (kTF32) umma_tf32(tacc, sdesc_step(ad, k), sdesc_step(bd, k), id, en);
+            else umma_f16(tacc, sdesc_step(ad, k), sdesc_step(bd, k), id, en);
+        }
+        umma_commit(&r.empty[s]);
+    }
+    return true;
+}
+
+// One split-TF32 tile: every k-block (hi unit, lo unit) is its own phase in the next
+// accumulator, flushed by the epilogue into round-to-nearest FP32 registers.
+PSVD_DEV bool mma_tile_x3(MmaRing &r, int nkb, uint32_t tmem, uint64_t *acc_full, uint64_t *acc_empty, uint32_t &q,
+                          uint32_t id) {
+    for (int kb = 0; kb < nkb; ++kb) {
+        const uint32_t buf = q & 1;
+        if (q >= 2 && !mbar_wait(&acc_empty[buf], ((q >> 1) - 1) & 1, r.err)) return false;
+        const uint32_t tacc = tmem + buf * kAccCols;
+        const uint32_t p0 = r.phase;
+        const uint32_t s0 = r.take();
+        const uint32_t p1 = r.phase;
+        const uint32_t s1 = r.take();
+        if (!mbar_wait(&r.full[s0], p0, r.err) || !mbar_wait(&r.full[s1], p1, r.err)) return false;
+        tc_fence_after();
+        const uint32_t a0 = r.base + s0 * r.unit_bytes, a1 = r.base + s1 * r.unit_bytes;
+        const uint64_t ahi = sdesc_k128(a0), bhi = sdesc_k128(a0 + kUnitA);
+        const uint64_t alo = sdesc_k128(a1), blo = sdesc_k128(a1 + kUnitA);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            umma_tf32(tacc, sdesc_step(alo, k), sdesc_step(bhi, k), id, k != 0);
+            umma_tf32(tacc, sdesc_step(ahi, k), sdesc_step(blo, k), id, 1);
+            umma_tf32(tacc, sdesc_step(ahi, k), sdesc_step(bhi, k), id, 1);
+        }
+        umma_commit(&r.empty[s0]);
+        umma_commit(&r.empty[s1]);
+        umma_commit(&acc_full[buf]);
+        ++q;
+    }
+    return true;
+}
+
 template <class Epi>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 gemm_tn_kernel(const __grid_constant__ GemmMaps maps, const GemmShape shp, Epi epi) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kUnitBytes);
-    uint64_t *empty = full + kStages;
-    uint64_t *acc_full = empty + kStages;      // [2] accumulator phase complete (tcgen05.commit)
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kRingBytes);
+    uint64_t *empty = full + kMaxStages;
+    uint64_t *acc_full = empty + kMaxStages;   // [2] accumulator phase complete (tcgen05.commit)
     uint64_t *acc_empty = acc_full + 2;        // [2] accumulator drained by the epilogue (8 warps)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
-    float *stage = reinterpret_cast<float *>(smem + kStages * kUnitBytes + 256);
+    float *stage = reinterpret_cast<float *>(smem + kRingBytes + 256);
     __shared__ volatile int s_abort;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bn = shp.bn;
+    const uint32_t unit_bytes = (uint32_t)(kUnitA + bn * 128);   // also the ring stride (1024-aligned)
+    const uint32_t nst = kRingBytes / unit_bytes;                // 4 or 6
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int s = 0; s < kMaxStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
         for (int i = 0; i < 2; ++i) { mbar_init(&acc_full[i], 1); mbar_init(&acc_empty[i], kEpiWarps); }
         fence_barrier_init();
         s_abort = 0;
@@ -154,33 +234,32 @@ gemm_tn_kernel(const __grid_constant__ GemmMaps maps, const GemmShape shp, Epi e
 
     const int tpm = tiles_per_matrix(shp);
     const int total = tpm * (shp.ksplit > 1 ? shp.ksplit : 1) * shp.batch;
-    const int bn = shp.bn;
-    const uint32_t unit_bytes = (uint32_t)(kUnitA + bn * 128);
 
     if (warp == kEpiWarps) {
         // ------------------------------------------------------------ TMA producer
+        // The ring position (stage) and its parity advance by counting: this thread and the
+        // MMA issuer sit on the tensor pipe's critical path, where even an integer division
+        // per k-block shows up in the MMA rate.
         if (lane == 0) {
-            uint32_t u = 0;
+            uint32_t ps = 0, pphase = 0;
             for (int t = blockIdx.x; t < total && !s_abort; t += gridDim.x) {
                 const TileJob jb = tile_job(shp, t, tpm);
                 const int b = jb.b, prec = jb.prec, nkb = jb.nkb;
                 if (shp.skip && shp.skip[b]) continue;
                 const int row_a = jb.ti * kBM, row_b = jb.tj * bn;
+                const CUtensorMap *ma0 = &maps.a_hi, *mb0 = &maps.b_hi, *ma1 = &maps.a_lo, *mb1 = &maps.b_lo;
+                if (prec == PREC_BF16) { ma0 = &maps.a_bf16; mb0 = &maps.b_bf16; }
+                const int kstep = prec == PREC_BF16 ? 64 : 32;
+                const int nu = prec == PREC_TF32X3 ? 2 : 1;
                 for (int kb = 0; kb < nkb; ++kb) {
-                    const int nu = prec == PREC_TF32X3 ? 2 : 1;
-                    for (int h = 0; h < nu; ++h, ++u) {
-                        const int s = u % kStages;
-                        if (!mbar_wait(&empty[s], ((u / kStages) & 1) ^ 1, shp.err)) { s_abort = 1; break; }
-                        uint8_t *st = smem + s * kUnitBytes;
-                        mbar_arrive_expect_tx(&full[s], unit_bytes);
-                        const CUtensorMap *ma, *mb;
-                        int k0;
-                        const int kg = jb.kb0 + kb;
-                        if (prec == PREC_BF16) { ma = &maps.a_bf16; mb = &maps.b_bf16; k0 = kg * 64; }
-                        else if (prec == PREC_TF32) { ma = &maps.a_hi; mb = &maps.b_hi; k0 = kg * 32; }
-                        else { ma = h ? &maps.a_lo : &maps.a_hi; mb = h ? &maps.b_lo : &maps.b_hi; k0 = kg * 32; }
-                        tma_load_3d(st, ma, &full[s], k0, row_a, b);
-                        tma_load_3d(st + kUnitA, mb, &full[s], k0, row_b, b);
+                    const int k0 = (jb.kb0 + kb) * kstep;
+                    for (int h = 0; h < nu; ++h) {
+                        if (!mbar_wait(&empty[ps], pphase ^ 1, shp.err)) { s_abort = 1; break; }
+                        uint8_t *st = smem + ps * unit_bytes;
+                        mbar_arrive_expect_tx(&full[ps], unit_bytes);
+                        tma_load_3d(st, h ? ma1 : ma0, &full[ps], k0, row_a, b);
+                        tma_load_3d(st + kUnitA, h ? mb1 : mb0, &full[ps], k0, row_b, b);
+                        if (++ps == nst) { ps = 0; pphase ^= 1; }
                     }
                     if (s_abort) break;
                 }
@@ -191,56 +270,23 @@ gemm_tn_kernel(const __grid_constant__ GemmMaps maps, const GemmShape shp, Epi e
         if (lane == 0) {
             const uint32_t id_tf32 = idesc_f32acc(kFmtTF32, kBM, bn);
             const uint32_t id_bf16 = idesc_f32acc(kFmtBF16, kBM, bn);
-            uint32_t u = 0, q = 0;
+            MmaRing ring{smem_u32(smem), unit_bytes, nst, full, empty, shp.err, 0u, 0u};
+            uint32_t q = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
                 const TileJob jb = tile_job(shp, t, tpm);
-                const int b = jb.b, prec = jb.prec, nkb = jb.nkb;
-                if (shp.skip && shp.skip[b]) continue;
-                const bool x3 = prec == PREC_TF32X3;
-                for (int kb = 0; kb < nkb && ok; ++kb) {
-                    const bool phase_start = x3 || kb == 0;
-                    const bool phase_end = x3 || kb == nkb - 1;
+                if ((shp.skip && shp.skip[jb.b]) || jb.nkb <= 0) continue;
+                if (jb.prec == PREC_TF32X3) {
+                    ok = mma_tile_x3(ring, jb.nkb, tmem, acc_full, acc_empty, q, id_tf32);
+                } else {
                     const uint32_t buf = q & 1;
-                    if (phase_start && q >= 2 && !mbar_wait(&acc_empty[buf], ((q >> 1) - 1) & 1, shp.err)) {
-                        ok = false; break;
-                    }
+                    if (q >= 2 && !mbar_wait(&acc_empty[buf], ((q >> 1) - 1) & 1, shp.err)) { ok = false; break; }
                     const uint32_t tacc = tmem + buf * kAccCols;
-                    const int s0 = u % kStages;
-                    if (!mbar_wait(&full[s0], (u / kStages) & 1, shp.err)) { ok = false; break; }
-                    int s1 = s0;
-                    if (x3) {
-                        s1 = (u + 1) % kStages;
-                        if (!mbar_wait(&full[s1], ((u + 1) / kStages) & 1, shp.err)) { ok = false; break; }
-                    }
-                    tc_fence_after();
-                    const uint32_t a0 = smem_u32(smem + s0 * kUnitBytes), b0 = a0 + kUnitA;
-                    const uint32_t a1 = smem_u32(smem + s1 * kUnitBytes), b1 = a1 + kUnitA;
-                    if (x3) {
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const uint64_t ahi = sdesc_k128(a0 + 32 * k), bhi = sdesc_k128(b0 + 32 * k);
-                            const uint64_t alo = sdesc_k128(a1 + 32 * k), blo = sdesc_k128(b1 + 32 * k);
-                            umma_tf32(tacc, alo, bhi, id_tf32, k != 0);
-                            umma_tf32(tacc, ahi, blo, id_tf32, 1);
-                            umma_tf32(tacc, ahi, bhi, id_tf32, 1);
-                        }
-                        umma_commit(&empty[s0]);
-                        umma_commit(&empty[s1]);
-                        u += 2;
-                    } else {
-                        const uint32_t id = prec == PREC_TF32 ? id_tf32 : id_bf16;
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const uint64_t ad = sdesc_k128(a0 + 32 * k), bd = sdesc_k128(b0 + 32 * k);
-                            const uint32_t en = (!phase_start) || k != 0;
-                            if (prec == PREC_TF32) umma_tf32(tacc, ad, bd, id, en);
-                            else umma_f16(tacc, ad, bd, id, en);
-                        }
-                        umma_commit(&empty[s0]);
-                        u += 1;
-                    }
-                    if (phase_end) { umma_commit(&acc_full[buf]); ++q; }
+                    ok = jb.prec == PREC_TF32 ? mma_tile<true>(ring, jb.nkb, tacc, id_tf32)
+                                              : mma_tile<false>(ring, jb.nkb, tacc, id_bf16);
+                    if (!ok) break;
+                    umma_commit(&acc_full[buf]);
+                    ++q;
                 }
             }
             if (!ok) {
