@@ -126,6 +126,11 @@ PSVD_DEV TileJob tile_job(const GemmShape &s, int t, int tpm) {
 // of a warp covers two rows x 16 consecutive columns instead of 32 rows x 1 column.
 template <class E, class = void> struct EpiHasElem : std::false_type {};
 template <class E> struct EpiHasElem<E, std::void_t<decltype(E::kElem)>> : std::integral_constant<bool, E::kElem> {};
+// Staged epilogues that also write a transposed copy define trans(acc, b, r, c0, v[16]):
+// it runs on the thread's own row (lanes = consecutive rows, so the transposed stores of a
+// warp are coalesced) next to the staged row-major element pass.
+template <class E, class = void> struct EpiHasTrans : std::false_type {};
+template <class E> struct EpiHasTrans<E, std::void_t<decltype(E::kTrans)>> : std::integral_constant<bool, E::kTrans> {};
 
 // Consumer side of the operand ring, as seen by the MMA issuer: shared-memory address of
 // unit 0, unit size, unit count, barriers, and the position of the next unit with the
@@ -357,6 +362,12 @@ gemm_tn_kernel(const __grid_constant__ GemmMaps maps, const GemmShape shp, Epi e
                                 epi.elem(ea, be, r0 + rr, cbase + c + cc, sw[rr * kStageRow + cc]);
                             }
                             __syncwarp();
+                            if constexpr (EpiHasTrans<Epi>::value) {
+                                float v[16];
+#pragma unroll
+                                for (int i = 0; i < 16; ++i) v[i] = acc[c + i];
+                                epi.trans(ea, be, r, cbase + c, v);
+                            }
                         }
                     }
                 }

@@ -141,7 +141,8 @@ PSVD_DEV void store_prec(int p, long long o, float x, __nv_bfloat16 *p16, float 
 // Gram tile G = X^T X (tiles reaching the upper triangle): every entry with col >= row
 // adds to ||G - I||_F^2 (off-diagonal entries twice) and stores P = c1 I + c3 G and its
 // mirror in the precision of this step's apply; entries below the diagonal are left to
-// the tile that holds their mirror.
+// the tile that holds their mirror.  The row-major entries go through the staged
+// (coalesced) element pass, the mirrors through trans() on the thread's own row.
 struct EpiGram {
     int n, B;
     const float *coef;   // coef + k*B*2
@@ -150,27 +151,37 @@ struct EpiGram {
     __nv_bfloat16 *P16;
     float *Phi, *Plo;
     long long ldp;
-    struct Acc { double r; };
-    PSVD_DEV void begin(Acc &a) const { a.r = 0.0; }
-    PSVD_DEV void chunk(Acc &a, int b, int r, int c0, int ti, int tj, float (&v)[16]) const {
+    struct Acc { double r; int p; float c1, c3; };
+    static constexpr bool kElem = true, kTrans = true;
+    PSVD_DEV bool staged() const { return true; }
+    PSVD_DEV void begin(Acc &a) const { a.r = 0.0; a.p = -1; }
+    PSVD_DEV void load(Acc &a, int b) const {
+        if (a.p < 0) { a.p = prec[b]; a.c1 = coef[2 * b]; a.c3 = coef[2 * b + 1]; }
+    }
+    PSVD_DEV void elem(Acc &a, int b, int r, int c, float g) const {
+        if (r >= n || c >= n || c < r) return;
+        load(a, b);
+        const float d = g - (r == c ? 1.f : 0.f);
+        a.r += (r == c ? 1.0 : 2.0) * (double)d * d;
+        const float pv = a.c3 * g + (r == c ? a.c1 : 0.f);
+        store_prec(a.p, (long long)b * n * ldp + (long long)r * ldp + c, pv, P16, Phi, Plo);
+    }
+    PSVD_DEV void trans(Acc &a, int b, int r, int c0, float (&v)[16]) const {
         if (r >= n) return;
-        const int p = prec[b];
-        const float c1 = coef[2 * b], c3 = coef[2 * b + 1];
-        const long long base = (long long)b * n * ldp;
-        double acc = 0.0;
+        load(a, b);
+        const long long base = (long long)b * n * ldp + r;
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             const int c = c0 + i;
             if (c >= n) break;
-            if (c < r) continue;
-            const float g = v[i];
-            const float d = g - (r == c ? 1.f : 0.f);
-            acc += (r == c ? 1.0 : 2.0) * (double)d * d;
-            const float pv = c3 * g + (r == c ? c1 : 0.f);
-            store_prec(p, base + (long long)r * ldp + c, pv, P16, Phi, Plo);
-            if (c != r) store_prec(p, base + (long long)c * ldp + r, pv, P16, Phi, Plo);
+            if (c <= r) continue;
+            store_prec(a.p, base + (long long)c * ldp, a.c3 * v[i], P16, Phi, Plo);
         }
-        a.r += acc;
+    }
+    PSVD_DEV void chunk(Acc &a, int b, int r, int c0, int, int, float (&v)[16]) const {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) elem(a, b, r, c0 + i, v[i]);
+        trans(a, b, r, c0, v);
     }
     PSVD_DEV void finish(Acc &a, int b, int, int) const {
         const double s = warp_sum(a.r);
@@ -178,27 +189,38 @@ struct EpiGram {
     }
 };
 
-// X_{k+1} = X_k P_k: stored row-major and transposed in the next step's precision.
+// X_{k+1} = X_k P_k: stored row-major (staged, coalesced) and transposed (trans(), lanes
+// on consecutive rows) in the next step's precision.
 struct EpiApply {
     int m, n, B;
     const int *prec_next;   // prec + (k+1)*B
     __nv_bfloat16 *X16, *XT16;
     float *Xhi, *Xlo, *XThi, *XTlo;
     long long ldn, ldm;
-    struct Acc {};
-    PSVD_DEV void begin(Acc &) const {}
-    PSVD_DEV void chunk(Acc &, int b, int r, int c0, int, int, float (&v)[16]) const {
+    struct Acc { int p; };
+    static constexpr bool kElem = true, kTrans = true;
+    PSVD_DEV bool staged() const { return true; }
+    PSVD_DEV void begin(Acc &a) const { a.p = -1; }
+    PSVD_DEV void elem(Acc &a, int b, int r, int c, float x) const {
+        if (r >= m || c >= n) return;
+        if (a.p < 0) a.p = prec_next[b];
+        store_prec(a.p, (long long)b * m * ldn + (long long)r * ldn + c, x, X16, Xhi, Xlo);
+    }
+    PSVD_DEV void trans(Acc &a, int b, int r, int c0, float (&v)[16]) const {
         if (r >= m) return;
-        const int p = prec_next[b];
-        const long long rb = (long long)b * m * ldn + (long long)r * ldn;
+        if (a.p < 0) a.p = prec_next[b];
         const long long tb = (long long)b * n * ldm + r;
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             const int c = c0 + i;
             if (c >= n) break;
-            store_prec(p, rb + c, v[i], X16, Xhi, Xlo);
-            store_prec(p, tb + (long long)c * ldm, v[i], XT16, XThi, XTlo);
+            store_prec(a.p, tb + (long long)c * ldm, v[i], XT16, XThi, XTlo);
         }
+    }
+    PSVD_DEV void chunk(Acc &a, int b, int r, int c0, int, int, float (&v)[16]) const {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) elem(a, b, r, c0 + i, v[i]);
+        trans(a, b, r, c0, v);
     }
     PSVD_DEV void finish(Acc &, int, int, int) const {}
 };
