@@ -195,10 +195,10 @@ def main():
     Fp = torch.empty(1, 8, device=dev)
     wsk = P._workspace(L.psvd_sketch_workspace_bytes(1, N, N, nprobe), dev)
 
-    def make(precision, learned=False):
+    def make(precision, learned=False, schedule=None):
         lb = torch.full((1,), 0.5, device=dev)
-        o = P.make_opts(precision=precision, schedule=P.SCHED_LEARNED if learned else P.SCHED_CANS,
-                        lower_bound=lb if learned else None)
+        sched = schedule if schedule is not None else (P.SCHED_LEARNED if learned else P.SCHED_CANS)
+        o = P.make_opts(precision=precision, schedule=sched, lower_bound=lb if learned else None)
         U = torch.empty(1, N, N, device=dev)
         S = torch.empty(1, N, device=dev)
         VT = torch.empty(1, N, N, device=dev)
@@ -262,11 +262,13 @@ def main():
     # accuracy of this very run (factors of the timed input against its known spectrum)
     info_m = P.info_dict(mixed[5])[0]
 
-    def accuracy(bufs):
+    def accuracy(bufs, a_in=None, spec=None):
         _, U, S, VT, *_ = bufs
-        u, sg, vt, a = U[0].double(), S[0].double(), VT[0].double(), A[0].double()
+        a_in = A if a_in is None else a_in
+        spec = s0 if spec is None else spec
+        u, sg, vt, a = U[0].double(), S[0].double(), VT[0].double(), a_in[0].double()
         eye = torch.eye(N, dtype=torch.float64, device=dev)
-        return {"sigma_err_rel_smax": float((sg.cpu() - torch.from_numpy(s0)).abs().max() / s0[0]),
+        return {"sigma_err_rel_smax": float((sg.cpu() - torch.from_numpy(spec)).abs().max() / spec[0]),
                 "recon": float(torch.linalg.matrix_norm(a - (u * sg) @ vt) / torch.linalg.matrix_norm(a)),
                 "ortho_u": float(torch.linalg.matrix_norm(u.T @ u - eye) / N ** 0.5),
                 "ortho_v": float(torch.linalg.matrix_norm(vt @ vt.T - eye) / N ** 0.5)}
@@ -352,6 +354,51 @@ def main():
         e2e.append((time.perf_counter() - t0) * 1e3)
     e2e_ms = float(np.median(e2e))
 
+    # reported beside the headline, outside its timed region: the same construction at the
+    # other condition numbers of the study (both paths) and the classical Newton-Schulz
+    # schedule on the headline matrix
+    def timed_on(bufs, a_in):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step(bufs, a_in)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    def path_report(bufs, a_in, spec):
+        step(bufs, a_in)
+        ts = [timed_on(bufs, a_in) for _ in range(2)]
+        inf = P.info_dict(bufs[5])[0]
+        return {"median_ms": float(np.median(ts)), "accuracy": accuracy(bufs, a_in, spec),
+                "polar_steps": [inf["steps_bf16"], inf["steps_tf32"], inf["steps_3xtf32"]],
+                "status": inf["status"], "sched_fallback": inf["sched_fallback"],
+                "prec_fallback": inf["prec_fallback"], "qr_fallback": inf["qr_fallback"]}
+
+    def extra_reports():
+        gen = torch.Generator()
+        gen.manual_seed(1000 + rank)                       # the headline matrix's factors
+        q1 = W.torch_orthonormal(gen, N, N).to(dev)
+        q2 = W.torch_orthonormal(gen, N, N).to(dev)
+        sweep = []
+        for kappa in (1e2, 1e3, 1e4, 1e6):
+            spec = W.kappa_spectrum(N, kappa)
+            a_k = ((q1 * torch.from_numpy(spec).to(dev)[None, :]) @ q2.T).float()[None].contiguous()
+            sweep.append({"kappa": kappa, "mixed": path_report(mixed, a_k, spec),
+                          "plain": path_report(plain, a_k, spec)})
+            del a_k
+        del q1, q2
+        ns = make(P.PREC_FP32, schedule=P.SCHED_NS)
+        ns_rep = path_report(ns, A, s0)
+        del ns
+        return {"kappa_sweep": sweep, "classical_ns_plain": ns_rep}
+
+    try:
+        reports = extra_reports()
+    except Exception as exc:          # a report must not cost the headline line
+        reports = {"error": f"{type(exc).__name__}: {exc}"}
+
     if rank == 0:
         line = {"metric": METRIC, "value": ms_mixed / ws, "unit": "ms", "n_gpus": ws, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms_mixed, "higher_is_better": False,
@@ -379,7 +426,8 @@ def main():
                 "clocks": clk.summary(),
                 "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": N * N * 4,
                         "d2h_bytes_per_step": N * N * 4 + N * 4},
-                "gpu_launches": int(launches)}
+                "gpu_launches": int(launches),
+                "reports": reports}
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline_leg()
         print(json.dumps(line), flush=True)

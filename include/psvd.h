@@ -108,6 +108,14 @@ typedef struct psvd_info {
 #define PSVD_MIXED_CORR_MAX 2e-3
 #define PSVD_MIXED_RANGE_MAX 5e-6
 
+/* PSVD_PREC_MIXED with the learned schedule: a matrix whose lower bound (opts.lower_bound,
+ * in units of X0 = M / sqrt(||M||_1 ||M||_inf)) is below PSVD_MIXED_LB_MIN starts on the
+ * 3xTF32 rung.  TF32 steps at such small singular values leave corrections above
+ * PSVD_MIXED_CORR_MAX, and the matrix would be recomputed anyway (measured at n = 4096:
+ * kappa = 1e2 keeps its TF32 result, kappa = 1e3 and above fall back).  steps_tf32 = 0
+ * in psvd_info shows that the gate applied. */
+#define PSVD_MIXED_LB_MIN 5e-5
+
 /* ---- workspace queries ---------------------------------------------------- */
 size_t psvd_polar_workspace_bytes(int64_t batch, int64_t m, int64_t n, const psvd_opts *opts);
 size_t psvd_svd_workspace_bytes(int64_t batch, int64_t m, int64_t n, const psvd_opts *opts);

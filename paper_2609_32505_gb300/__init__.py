@@ -44,6 +44,7 @@ INFO_INTS = 8   # the first 8 fields are int32, the rest float32
 INFO_WORDS = len(INFO_FIELDS)
 MIXED_CORR_MAX = 2e-3    # PSVD_MIXED_CORR_MAX of psvd.h
 MIXED_RANGE_MAX = 5e-6   # PSVD_MIXED_RANGE_MAX of psvd.h
+MIXED_LB_MIN = 5e-5      # PSVD_MIXED_LB_MIN of psvd.h
 
 
 def build(force: bool = False) -> str:

@@ -102,9 +102,11 @@ struct CoefTable {
 };
 
 // coef[(k * B + b) * 2 + {0,1}] for k < K.  Learned: greedy optimal cubics from
-// [l_b, 1] per matrix (FP64), and the step budget before the conservative rerun.
+// [l_b, 1] per matrix (FP64), and the step budget before the conservative rerun; with
+// gate_x3, a matrix whose bound is below PSVD_MIXED_LB_MIN starts on the split-TF32 rung.
 __global__ void schedule_fill_kernel(int B, int K, CoefTable tab, const float *lower, int learned, double tol,
-                                     int budget_opt, const int *active, float *coef, int *budget) {
+                                     int budget_opt, const int *active, float *coef, int *budget, int gate_x3,
+                                     int *prec) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     if (active && !active[b]) return;
@@ -118,6 +120,7 @@ __global__ void schedule_fill_kernel(int B, int K, CoefTable tab, const float *l
         return;
     }
     double l = (double)lower[b];
+    if (gate_x3 && !(l >= PSVD_MIXED_LB_MIN)) prec[b] = PREC_TF32X3;
     if (!(l > 1e-12)) l = 1e-12;
     if (l > 0.999) l = 0.999;
     double lo = l, hi = 1.0;
@@ -473,8 +476,10 @@ int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &
     std::vector<Cubic> sched = o.schedule == PSVD_SCHED_NS ? std::vector<Cubic>(1, Cubic{1.5, -0.5, 0.0}) : cons;
     tab.len = (int)sched.size();
     for (int i = 0; i < tab.len; ++i) { tab.c1[i] = (float)sched[i].c1; tab.c3[i] = (float)sched[i].c3; }
+    const int gate_x3 = learned && w.mixed && !w.bf16 ? 1 : 0;
     schedule_fill_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, w.kcap + 1, tab, o.lower_bound, learned ? 1 : 0,
-                                                          o.tol, o.budget, nullptr, w.coef, w.budget);
+                                                          o.tol, o.budget, nullptr, w.coef, w.budget, gate_x3,
+                                                          w.prec);
     count_launch(1);
     if (int rc = prepare_x0(A, w, st, nullptr)) return rc;   // zero matrices get X0 = 0
     if (want_h) {
@@ -497,7 +502,7 @@ int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &
             ct.len = (int)cons.size();
             for (int i = 0; i < ct.len; ++i) { ct.c1[i] = (float)cons[i].c1; ct.c3[i] = (float)cons[i].c3; }
             schedule_fill_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, w.kcap + 1, ct, nullptr, 0, o.tol, 0,
-                                                                  w.fallback, w.coef, w.budget);
+                                                                  w.fallback, w.coef, w.budget, 0, w.prec);
             count_launch(1);
             if (cudaMemsetAsync(w.res, 0, sizeof(double) * (size_t)(w.kcap + 2) * B, st) ||
                 cudaMemsetAsync(w.notdone, 0, sizeof(int) * (size_t)(w.kcap + 2), st))
