@@ -152,3 +152,33 @@ def test_mixed_range_check_on_tall_input():
     _fallback_consistent(info)
     assert info[0]["range_resid"] > 0
     _gates(a, u, s, vt, O.svd(a)[1], 1)
+
+
+def test_mixed_learned_gate_on_small_lower_bound():
+    # PSVD_MIXED_LB_MIN: with the learned schedule, a matrix whose lower bound is below the
+    # threshold starts on the split-TF32 rung (no TF32 step, nothing to recompute); one with
+    # a larger bound makes its TF32 attempt.  Batch of two: kappa = 1e3 with a bound below
+    # the threshold, kappa = 10 with a bound above it; both bounds are valid (<= sigma_min(X0)).
+    import paper_2609_32505_gb300 as P
+    n = 512
+    mats = [W.constructed(21, n, n, W.kappa_spectrum(n, k))[0].astype(np.float32).astype(np.float64)
+            for k in (1e3, 10.0)]
+    lbs = []
+    for a in mats:
+        scale = np.sqrt(np.abs(a).sum(0).max() * np.abs(a).sum(1).max())
+        lbs.append(0.5 * O.svd(a)[1][-1] / scale)          # half of sigma_min(X0)
+    lbs[0] = min(lbs[0], 0.5 * P.MIXED_LB_MIN)
+    assert lbs[0] < P.MIXED_LB_MIN <= lbs[1]
+    A = torch.from_numpy(np.stack(mats).astype(np.float32)).cuda()
+    lb = torch.tensor(lbs, dtype=torch.float32, device="cuda")
+    U, S, VT, info = P.svd_fwd(A, P.make_opts(precision=P.PREC_MIXED, schedule=P.SCHED_LEARNED, lower_bound=lb),
+                               return_info=True)
+    torch.cuda.synchronize()
+    _fallback_consistent(info)
+    assert info[0]["status"] == 0 and info[0]["sched_fallback"] == 0
+    assert info[0]["steps_tf32"] == 0 and info[0]["steps_bf16"] == 0 and info[0]["steps_3xtf32"] > 0
+    assert info[0]["prec_fallback"] == 0
+    assert info[1]["steps_tf32"] > 0 or info[1]["prec_fallback"] == 1
+    u, s, vt = U.cpu().double().numpy(), S.cpu().double().numpy(), VT.cpu().double().numpy()
+    for b, a in enumerate(mats):
+        _gates(a, u[b], s[b], vt[b], O.svd(a)[1], 1)
