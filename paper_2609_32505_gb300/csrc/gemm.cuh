@@ -8,8 +8,9 @@
 //
 // Persistent kernel: one CTA per SM walks a static list of output tiles of
 // 128 x BN (BN = 256, or 128 when N <= 128), UMMA M = 128, N = BN, cta_group::1.
-// 128-wide tiles cost about twice as much per flop as 256-wide ones on GB300 (measured:
-// BF16 at 8192^3, 559 against 1049 TFLOP/s), so they are used only where N <= 128.
+// 128-wide tiles cost about twice as much per flop as 256-wide ones on GB300 (a fixed
+// cost per MMA instruction; measured with one mainloop version, BF16 at 8192^3: 559
+// against 1049 TFLOP/s), so they are used only where N <= 128.
 // Shared memory holds a 192 KB ring of units (4 x 48 KB at BN = 256, 6 x 32 KB at
 // BN = 128), each one TMA'd k-block: an A sub-tile (128 rows x 128 B) and a B sub-tile
 // (BN rows x 128 B), both in the canonical 128-byte-swizzled K-major layout:

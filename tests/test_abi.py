@@ -77,3 +77,28 @@ def test_workspace_queries_scale(lib):
     assert lib.psvd_svd_bwd_workspace_bytes(1, 300, 200) > 0
     assert lib.psvd_eigh_workspace_bytes(3, 100) > lib.psvd_eigh_workspace_bytes(1, 100)
     assert lib.psvd_svd_workspace_bytes(0, 4, 4, ctypes.byref(o)) == 0
+
+
+def _header():
+    txt = open(os.path.join(ROOT, "include", "psvd.h")).read()
+    defines = {k: float(v) for k, v in re.findall(r"#define\s+(PSVD_[A-Z0-9_]+)\s+(-?[0-9.eE+-]+)\b", txt)}
+    body = re.search(r"typedef struct psvd_info \{(.*?)\} psvd_info;", txt, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(int|float)\s+([a-z0-9_]+)\s*;", body)
+    return defines, fields
+
+
+def test_python_mirrors_of_header_constants():
+    # the binding's copies of the header's codes and thresholds, and the psvd_info layout
+    # the binding decodes (its int fields first, then its float fields)
+    import paper_2609_32505_gb300 as P
+    d, fields = _header()
+    assert (P.PREC_FP32, P.PREC_MIXED, P.PREC_MIXED_BF16) == (d["PSVD_PREC_FP32"], d["PSVD_PREC_MIXED"],
+                                                              d["PSVD_PREC_MIXED_BF16"])
+    assert (P.SCHED_CANS, P.SCHED_LEARNED, P.SCHED_NS) == (d["PSVD_SCHED_CANS"], d["PSVD_SCHED_LEARNED"],
+                                                           d["PSVD_SCHED_NS"])
+    assert P.MIXED_CORR_MAX == d["PSVD_MIXED_CORR_MAX"]
+    assert P.MIXED_RANGE_MAX == d["PSVD_MIXED_RANGE_MAX"]
+    assert P.MIXED_LB_MIN == d["PSVD_MIXED_LB_MIN"]
+    assert [name for _, name in fields] == P.INFO_FIELDS
+    assert [t for t, _ in fields] == ["int"] * P.INFO_INTS + ["float"] * (P.INFO_WORDS - P.INFO_INTS)
