@@ -827,17 +827,22 @@ struct EpiSubSplit {
     float *hi, *lo;
     long long ld, bs;
     struct Acc {};
-    static constexpr bool kElem = true;
+    static constexpr bool kElem = true, kPre = true;
     PSVD_DEV bool staged() const { return true; }
-    PSVD_DEV void elem(Acc &, int b, int r, int c, float v) const {
+    PSVD_DEV float pre(int b, int r, int c) const {
+        if (r >= rows || c >= cols) return 0.f;
+        const long long o = b * bs + (long long)r * ld + c;
+        return hi[o] + lo[o];
+    }
+    PSVD_DEV void elem_pre(Acc &, int b, int r, int c, float v, float p) const {
         if (r >= rows || c >= cols) return;
         const long long o = b * bs + (long long)r * ld + c;
-        const float x = (hi[o] + lo[o]) - v;
         float h, l;
-        split_tf32(x, h, l);
+        split_tf32(p - v, h, l);
         hi[o] = h;
         lo[o] = l;
     }
+    PSVD_DEV void elem(Acc &a, int b, int r, int c, float v) const { elem_pre(a, b, r, c, v, pre(b, r, c)); }
     PSVD_DEV void begin(Acc &) const {}
     PSVD_DEV void chunk(Acc &, int b, int r, int c0, int, int, float (&v)[16]) const {
         if (r >= rows) return;

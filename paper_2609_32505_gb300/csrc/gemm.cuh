@@ -132,6 +132,12 @@ template <class E> struct EpiHasElem<E, std::void_t<decltype(E::kElem)>> : std::
 // warp are coalesced) next to the staged row-major element pass.
 template <class E, class = void> struct EpiHasTrans : std::false_type {};
 template <class E> struct EpiHasTrans<E, std::void_t<decltype(E::kTrans)>> : std::integral_constant<bool, E::kTrans> {};
+// Read-modify-write epilogues define pre(b, r, c) (the value read at (r, c)) and
+// elem_pre(acc, b, r, c, v, p): the staged pass issues the 16 reads of a chunk before its
+// first store, since stores to the array being read would otherwise order every read
+// after the previous element's store (one read in flight per thread).
+template <class E, class = void> struct EpiHasPre : std::false_type {};
+template <class E> struct EpiHasPre<E, std::void_t<decltype(E::kPre)>> : std::integral_constant<bool, E::kPre> {};
 
 // Consumer side of the operand ring, as seen by the MMA issuer: shared-memory address of
 // unit 0, unit size, unit count, barriers, and the position of the next unit with the
@@ -357,10 +363,21 @@ gemm_tn_kernel(const __grid_constant__ GemmMaps maps, const GemmShape shp, Epi e
 #pragma unroll
                             for (int i = 0; i < 16; ++i) sw[lane * kStageRow + i] = acc[c + i];
                             __syncwarp();
+                            if constexpr (EpiHasPre<Epi>::value) {
+                                float pv[16];
+#pragma unroll
+                                for (int k = 0; k < 16; ++k) pv[k] = epi.pre(be, r0 + 2 * k + rr0, cbase + c + cc);
+#pragma unroll
+                                for (int k = 0; k < 16; ++k) {
+                                    const int rr = 2 * k + rr0;
+                                    epi.elem_pre(ea, be, r0 + rr, cbase + c + cc, sw[rr * kStageRow + cc], pv[k]);
+                                }
+                            } else {
 #pragma unroll 4
-                            for (int k = 0; k < 16; ++k) {
-                                const int rr = 2 * k + rr0;
-                                epi.elem(ea, be, r0 + rr, cbase + c + cc, sw[rr * kStageRow + cc]);
+                                for (int k = 0; k < 16; ++k) {
+                                    const int rr = 2 * k + rr0;
+                                    epi.elem(ea, be, r0 + rr, cbase + c + cc, sw[rr * kStageRow + cc]);
+                                }
                             }
                             __syncwarp();
                             if constexpr (EpiHasTrans<Epi>::value) {
