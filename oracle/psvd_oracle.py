@@ -34,7 +34,7 @@ What each function computes, with the passage it follows:
 * ``sketch_features`` / ``mlp_*``  the learned lower-bound predictor's features and
                            a plain FP64 MLP (8 -> 64 -> 64 -> 1) forward/backward.
 
-Readings where the paper is silent or garbled (each listed in the design doc):
+Readings taken where the paper is silent or garbled:
 the closed-form CANS cubic and the bisection reading of the preprocessing;
 stopping residual ||X^T X - I||_F / sqrt(n); skew(X) = (X - X^T)/2; the sign of the
 (I - U U^T) Ubar S^-1 V^T term is '+' (Theorem G.1); eigenvector sign convention;

@@ -15,7 +15,7 @@ def pytest_configure(config):
 
 def pytest_collection_modifyitems(config, items):
     # Without a GPU, GPU tests are skipped rather than failing on the missing device;
-    # the driver selects them explicitly with -m gpu on a GPU machine.
+    # on a machine with a GPU they are selected with -m gpu.
     try:
         import torch
         have_gpu = torch.cuda.is_available()
