@@ -80,7 +80,7 @@ void psvd_default_opts(psvd_opts *o);
 typedef struct psvd_info {
     int   status;          /* PSVD_OK, PSVD_NOT_CONVERGED or PSVD_ERR_NONFINITE         */
     int   iters;           /* polynomial steps applied                                  */
-    int   qr_fallback;     /* 1 if U was re-orthogonalized by QR (Algorithm 1 step 8)    */
+    int   qr_fallback;     /* 1 if U was re-orthogonalized by QR (Algorithm 1's QR fallback) */
     int   sched_fallback;  /* 1 if the learned schedule missed tol and the conservative
                               schedule was rerun                                          */
     int   prec_fallback;   /* svd_fwd, mixed precision: 1 if the eigenbasis correction
@@ -125,7 +125,7 @@ size_t psvd_eigh_workspace_bytes(int64_t batch, int64_t n);
 
 /* ---- forward ----------------------------------------------------------------
  * psvd_polar_fwd -- right polar decomposition M = W H (Definition 2.1) by
- *   Algorithm 1 steps 1-4: W (m x n, W^T W = I) and H = (W^T M)_sym (n x n, FP64
+ *   Algorithm 1, polar-factor part: W (m x n, W^T W = I) and H = (W^T M)_sym (n x n, FP64
  *   symmetrization, stored FP32).  A: batch x m x n input (read only).
  *   W: batch x m x n out.  H: batch x n x n out (may be NULL).  info: batch records.
  */
@@ -157,7 +157,7 @@ int psvd_svd_fwd(const float *A, float *U, float *S, float *VT, int64_t batch, i
                  int64_t n, const psvd_opts *opts, void *ws, size_t ws_bytes,
                  psvd_info *info, void *stream);
 
-/* psvd_eigh -- symmetric EVD H = V diag(S) V^T (Algorithm 1 step 5) of a batch of
+/* psvd_eigh -- symmetric EVD H = V diag(S) V^T (the EVD of Algorithm 1) of a batch of
  *   n x n symmetric matrices (only the upper triangle is read).  S descending,
  *   VT rows = eigenvectors with the sign convention above. */
 int psvd_eigh(const float *Hs, float *S, float *VT, int64_t batch, int64_t n,

@@ -20,7 +20,7 @@ What each function computes, with the passage it follows:
                            Newton-Schulz iteration X <- X (3 I - X^T X) / 2 (Section 3,
                            Appendix A.1), run to FP64 convergence.
 * ``polar_cans``           the same limit by the CANS schedule (Algorithm 1, steps 2-3).
-* ``eigh``                 cyclic Jacobi EVD (Algorithm 1, step 5), sigma descending,
+* ``eigh``                 cyclic Jacobi EVD (the EVD of Algorithm 1), sigma descending,
                            each eigenvector's largest-magnitude entry made positive.
 * ``qr_nonneg``            QR with non-negative diag(R) (Appendix A.2).
 * ``svd``                  Algorithm 1 end to end with the FP64 pieces above.

@@ -1,4 +1,4 @@
-// Symmetric eigendecomposition H = V Sigma V^T (Algorithm 1 step 5), in four stages:
+// Symmetric eigendecomposition H = V Sigma V^T (the EVD of Algorithm 1), in four stages:
 //  1. Householder tridiagonalization Q^T H Q = T (FP32, persistent cooperative kernel,
 //     one group barrier per reflector; the row that the next reflector is built from
 //     is left un-updated and corrected on the fly, so the rank-2 update of step k and

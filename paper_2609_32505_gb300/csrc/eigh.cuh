@@ -1,4 +1,4 @@
-// Symmetric eigensolver for H = V Sigma V^T (Algorithm 1 step 5).
+// Symmetric eigensolver for H = V Sigma V^T (the EVD of Algorithm 1).
 #pragma once
 #include <algorithm>
 

@@ -1,4 +1,4 @@
-// Polar factor by polynomial iteration (Algorithm 1 steps 1-4), shared by
+// Polar factor by polynomial iteration (the polar-factor part of Algorithm 1), shared by
 // psvd_polar_fwd and psvd_svd_fwd.
 #pragma once
 #include "ops.cuh"
@@ -82,7 +82,7 @@ struct PolarWS {
 
 inline int polar_kcap(const psvd_opts &o) { return o.max_iter + (o.schedule == PSVD_SCHED_CANS ? o.pre_iters : 0); }
 
-// Runs Algorithm 1 steps 1-3 (normalize, schedule, iterate) for all matrices, then
+// Runs the iteration of Algorithm 1 (normalize, schedule, iterate) for all matrices, then
 // writes W (user layout, may be null) and leaves W^T split in XThi[0]/XTlo[0] and W
 // split in Xhi[0]/Xlo[0].  If `want_h`, also computes Hsym = (W^T M)_sym (FP64
 // averaging) and copies it to H_out (may be null).  Synchronizes the stream a few

@@ -462,7 +462,7 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
         bu_hi = VEt_hi;
         bu_lo = VEt_lo;
     }
-    // U = W (V E), with the column norms of Algorithm 1 step 7
+    // U = W (V E), with the column-norm check of Algorithm 1
     if (cudaMemsetAsync(w.colss, 0, sizeof(float) * (size_t)B * n, st)) return PSVD_ERR_CUDA;
     {
         EpiColNorm e;

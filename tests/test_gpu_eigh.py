@@ -1,4 +1,4 @@
-"""GPU symmetric eigensolver (Algorithm 1 step 5) against the FP64 oracle (cyclic Jacobi).
+"""GPU symmetric eigensolver (the EVD of Algorithm 1) against the FP64 oracle (cyclic Jacobi).
 
 Eigenvalues: |lambda_i - lambda_i*| <= 2e-6 ||H||_2 (FP32 Householder reduction is
 backward stable with error ~ sqrt(n) u ||H||).  Eigenvectors are unique only up to

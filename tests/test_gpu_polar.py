@@ -1,4 +1,4 @@
-"""GPU polar factor (Algorithm 1 steps 1-4) against the FP64 oracle.
+"""GPU polar factor (the polar-factor part of Algorithm 1) against the FP64 oracle.
 
 W is unique for full-rank inputs (Definition 2.1), so the CUDA path's W and H are
 compared element by element with the oracle's, whatever schedule reached them.
