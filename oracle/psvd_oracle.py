@@ -19,12 +19,16 @@ What each function computes, with the passage it follows:
 * ``polar_newton_schulz``  the unique polar factor of Definition 2.1 by the classical
                            Newton-Schulz iteration X <- X (3 I - X^T X) / 2 (Section 3,
                            Appendix A.1), run to FP64 convergence.
-* ``polar_cans``           the same limit by the CANS schedule (Algorithm 1, steps 2-3).
+* ``polar_cans``           the same limit by the CANS schedule (the iteration of Algorithm 1).
 * ``eigh``                 cyclic Jacobi EVD (the EVD of Algorithm 1), sigma descending,
                            each eigenvector's largest-magnitude entry made positive.
 * ``qr_nonneg``            QR with non-negative diag(R) (Appendix A.2).
 * ``svd``                  Algorithm 1 end to end with the FP64 pieces above.
 * ``svd_onesided``         an independent SVD route (Hestenes one-sided Jacobi).
+* ``svd_preqr`` / ``polar_preqr``  the QR preprocessing of rectangular inputs (Section 4.1,
+                           rectangular matrices): M = Q R (thin), the SVD or polar
+                           decomposition of the n x n factor R, then U = Q U_R, W = Q W_R,
+                           H = H_R.
 * ``polar_bwd``            Algorithm 3 / Proposition 3.2 (regularized), Theorem 3.1 (eps=0).
 * ``evd_bwd``              Theorem 4.3 (EVD pseudo-gradient).
 * ``svd_bwd``              Algorithm 4 (complete pipeline), kreg modes 0/1/2.
@@ -292,6 +296,26 @@ def svd(m: np.ndarray, eps_qr: float = 1e-10, polar: str = "ns"):
     if used_qr:
         u, _ = qr_nonneg(u)
     return u, sigma, v.T, {"qr": used_qr, "iters": it}
+
+
+def svd_preqr(m: np.ndarray, eps_qr: float = 1e-10, polar: str = "ns"):
+    """SVD of a rectangular M (m >= n) through its thin QR (Section 4.1, rectangular
+    matrices): M = Q R, R = U_R S V^T by Algorithm 1, U = Q U_R.  Returns (U, sigma, V^T,
+    info) like ``svd``."""
+    m = np.asarray(m, dtype=np.float64)
+    q, r = qr_nonneg(m)
+    u_r, sigma, vt, info = svd(r, eps_qr=eps_qr, polar=polar)
+    return q @ u_r, sigma, vt, info
+
+
+def polar_preqr(m: np.ndarray):
+    """Polar decomposition of a rectangular M (m >= n) through its thin QR: with M = Q R and
+    R = W_R H_R, the factor Q W_R has orthonormal columns and (Q W_R) H_R = M, so it is the
+    polar factor of M (unique for full rank, Definition 2.1) and H_R is H.  Returns (W, H)."""
+    m = np.asarray(m, dtype=np.float64)
+    q, r = qr_nonneg(m)
+    w_r, h_r, _ = polar_newton_schulz(r)
+    return q @ w_r, h_r
 
 
 def svd_onesided(m: np.ndarray, tol: float = 1e-15, max_sweeps: int = 100):

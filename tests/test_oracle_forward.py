@@ -287,3 +287,29 @@ def test_gram_evd_fails_sigma_tolerance():
     assert np.max(np.abs(sg - s)) > 1e-5 * s[0]
     u, sig, vt, _ = O.svd(a32.astype(np.float64))
     assert np.max(np.abs(sig - s)) < 1e-5 * s[0]
+
+
+def test_preqr_constructed_tall():
+    # the QR preprocessing of rectangular inputs (Section 4.1) on a constructed tall matrix:
+    # the spectrum, the polar factor Q1 Q2^T and H = Q2 diag(s) Q2^T are known exactly
+    m, n = 40, 12
+    s = W.kappa_spectrum(n, 1e3)
+    a, q1, q2 = W.constructed(31, m, n, s)
+    u, sg, vt, _ = O.svd_preqr(a)
+    assert np.abs(sg - s).max() <= 1e-12 * s[0]
+    np.testing.assert_allclose(u @ vt, q1 @ q2.T, atol=1e-11)
+    w, h = O.polar_preqr(a)
+    np.testing.assert_allclose(w, q1 @ q2.T, atol=1e-11)
+    np.testing.assert_allclose(h, (q2 * s) @ q2.T, atol=1e-12 * s[0])
+
+
+def test_preqr_agrees_with_direct_route():
+    # the QR route and Algorithm 1 on M itself give the same singular values and the same
+    # (unique) polar factor U V^T, and the QR route's factors reconstruct M
+    a = W.rng_for(32).standard_normal((50, 20))
+    u1, s1, vt1, _ = O.svd(a)
+    u2, s2, vt2, _ = O.svd_preqr(a)
+    assert np.abs(s1 - s2).max() <= 1e-12 * s1[0]
+    np.testing.assert_allclose(u1 @ vt1, u2 @ vt2, atol=1e-12)
+    assert O.recon_error(a, u2, s2, vt2) <= 1e-13
+    assert O.ortho_error(u2) <= 1e-13 and O.ortho_error(vt2.T) <= 1e-13
