@@ -5,7 +5,8 @@ consequences, central finite differences through the oracle's own forward
 (tiny generic inputs), Townsend's formula (Theorem G.1) on distinct spectra,
 Theorem H.1 on exactly repeated spectra for gauge-invariant losses, explicit
 factor paths at degenerate points (no SVD differentiated), the eps^(1/4) rate of
-Proposition 3.2, Lemma D.1 and Example C.1."""
+Proposition 3.2, Lemma D.1 and Example C.1; Theorem 4.3 (the EVD pseudo-gradient)
+against central finite differences."""
 import math
 
 import numpy as np
@@ -266,3 +267,34 @@ def test_table3_qualitative_gradient_norm():
     assert norms_r[0] == pytest.approx(norms_t[0], rel=1e-3)
     assert norms_t[2] > 100 * norms_t[0]
     assert norms_r[2] < 2 * norms_r[0]
+
+
+def test_evd_bwd_thm43_finite_differences():
+    # Theorem 4.3 on a symmetric matrix with distinct eigenvalues: the directional
+    # derivative of <Vbar, V> + <sbar, s> along a symmetric E (central differences through
+    # LAPACK's eigh with the oracle's sign convention, locally constant here) equals
+    # <Mbar*, E>; Mbar* is symmetric
+    rng = W.rng_for(51)
+    n = 7
+    g = rng.standard_normal((n, n))
+    a = (g + g.T) / 2
+    vbar = rng.standard_normal((n, n))
+    sbar = rng.standard_normal(n)
+
+    def fwd(x):
+        w, v = np.linalg.eigh(x)
+        order = np.argsort(-w, kind="stable")
+        return w[order], O.canonical_signs(v[:, order])
+
+    s, v = fwd(a)
+    assert np.min(np.abs(np.diff(s))) > 1e-2
+    mbar = O.evd_bwd(v, s, vbar, sbar)
+    np.testing.assert_allclose(mbar, mbar.T, atol=1e-13)
+    h = 1e-6
+    for _ in range(4):
+        e = rng.standard_normal((n, n))
+        e = (e + e.T) / 2
+        sp, vp = fwd(a + h * e)
+        sm, vm = fwd(a - h * e)
+        fd = (np.sum(vbar * (vp - vm)) + np.sum(sbar * (sp - sm))) / (2 * h)
+        assert abs(fd - np.sum(mbar * e)) <= 1e-7 * max(1.0, abs(fd)), (fd, np.sum(mbar * e))
