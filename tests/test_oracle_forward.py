@@ -84,8 +84,8 @@ def test_cans_small_a_limit():
 
 
 def test_cans_golden_values():
-    # self-consistency values of the closed form (our derivation; the CANS paper
-    # that defines the coefficients is not available), see the fixture header
+    # the minimax cubics solved as a linear program on a dense grid, with no closed form
+    # (tests/golden/make_cans_cubic.py), against the oracle's equioscillation closed form
     rows = np.loadtxt(os.path.join(GOLDEN, "cans_cubic.txt"))
     for a, b, c1, c3, e in rows:
         got = O.cans_cubic(a, b)
