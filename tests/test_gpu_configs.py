@@ -6,7 +6,8 @@ at any size: constructed inputs against their known spectrum with Weyl's bound f
 input rounding, reconstruction and orthogonality computed in FP64 on the device, and, for
 the Marchenko-Pastur batch, sampled matrices against LAPACK's FP64 singular values (the
 oracle's own SVD is pinned to LAPACK in tests/test_oracle_forward.py).  Where the oracle is
-fast enough (the 512 x 512 backward), sampled matrices are compared with it directly."""
+fast enough (the 512 x 512 backward), sampled matrices are compared with it directly, both
+sides taking the exact factors the generator built."""
 import numpy as np
 import pytest
 import torch
@@ -74,28 +75,36 @@ def test_config_weight_shaped_bf16_inputs():
 
 
 def test_config_clustered_backward_batch():
-    # 64 x (512 x 512) with 128 clusters of multiplicity 4; loss <W_U, U> + <w, sigma> +
-    # <W_V, V>: the Algorithm 4 gradient on the GPU factors against the FP64 oracle's
-    # Algorithm 4 on the same factors (sampled), eps = 1e-8
+    # 64 x (512 x 512) with 128 clusters of multiplicity 4.  Forward: the GPU spectrum
+    # against the known one.  Backward, loss <W_U, U> + <w, sigma> + <W_V, V>, eps = 1e-8:
+    # the Algorithm 4 gradient of the library and of the FP64 oracle (sampled), both fed
+    # the exact factors the matrices were built from (rounded to FP32)
     import paper_2609_32505_gb300 as P
     B, n = 64, 512
-    mats, specs = zip(*[W.clustered_square(300 + b, n) for b in range(B)])
-    a = np.stack(mats).astype(np.float32)
+    facs = [W.clustered_square_factors(300 + b, n) for b in range(B)]
+    specs = [f[2] for f in facs]
+    a = np.stack([f[0] for f in facs]).astype(np.float32)
     A = torch.from_numpy(a).cuda()
-    U, S, VT = P.svd_fwd(A, P.make_opts())
-    w = [W.loss_weights(300 + b, n, n) for b in range(B)]
-    GU = torch.from_numpy(np.stack([x[0] for x in w]).astype(np.float32)).cuda()
-    GS = torch.from_numpy(np.stack([x[1] for x in w]).astype(np.float32)).cuda()
-    GVT = torch.from_numpy(np.stack([x[2].T for x in w]).astype(np.float32)).cuda()
-    dA = P.svd_bwd(A, U, S, VT, GU, GS, GVT, eps=1e-8, kreg_mode=0)
+    _, S, _ = P.svd_fwd(A, P.make_opts())
     torch.cuda.synchronize()
     s = S.cpu().double().numpy()
     for b in range(B):
         assert np.abs(s[b] - specs[b]).max() <= 1e-5 * specs[b][0] + 1e-6
-    u, vt, g = U.cpu().double().numpy(), VT.cpu().double().numpy(), dA.cpu().double().numpy()
+    del S
+    u = np.stack([f[1] for f in facs]).astype(np.float32)
+    sx = np.stack(specs).astype(np.float32)
+    vt = np.ascontiguousarray(np.stack([f[3].T for f in facs])).astype(np.float32)
+    w = [W.loss_weights(300 + b, n, n) for b in range(B)]
+    GU = torch.from_numpy(np.stack([x[0] for x in w]).astype(np.float32)).cuda()
+    GS = torch.from_numpy(np.stack([x[1] for x in w]).astype(np.float32)).cuda()
+    GVT = torch.from_numpy(np.stack([x[2].T for x in w]).astype(np.float32)).cuda()
+    dA = P.svd_bwd(A, torch.from_numpy(u).cuda(), torch.from_numpy(sx).cuda(), torch.from_numpy(vt).cuda(),
+                   GU, GS, GVT, eps=1e-8, kreg_mode=0)
+    torch.cuda.synchronize()
+    g = dA.cpu().double().numpy()
     for b in (0, 17, 63):
-        ref = O.svd_bwd(a[b].astype(np.float64), u[b], s[b], vt[b], w[b][0], w[b][1], w[b][2].T, eps=1e-8,
-                        kreg_mode=0)
+        ref = O.svd_bwd(a[b].astype(np.float64), u[b].astype(np.float64), sx[b].astype(np.float64),
+                        vt[b].astype(np.float64), w[b][0], w[b][1], w[b][2].T, eps=1e-8, kreg_mode=0)
         assert np.linalg.norm(g[b] - ref) <= 1e-3 * np.linalg.norm(ref)
 
 

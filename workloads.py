@@ -58,6 +58,11 @@ def gap_spectrum(n: int, gap: float) -> np.ndarray:
     return s[::-1].copy()
 
 
+def linear_spectrum(n: int, lo: float = 0.1, hi: float = 1.0) -> np.ndarray:
+    """s_i linearly spaced from hi down to lo: well-separated singular values."""
+    return np.linspace(hi, lo, n)
+
+
 def loguniform_spectrum(rng: np.random.Generator, n: int, lo: float, hi: float) -> np.ndarray:
     return np.exp(rng.uniform(math.log(lo), math.log(hi), size=n))
 
@@ -88,11 +93,18 @@ def clustered_spectrum(rng: np.random.Generator, n_clusters: int, mult: int,
 # Named workloads (shapes and distributions of the paper's experiments)
 # --------------------------------------------------------------------------
 
-def small_square(seed: int = 1, n: int = 256):
-    """One n x n matrix with singular values log-uniform in [1e-3, 1]."""
+def small_square_factors(seed: int = 1, n: int = 256):
+    """One n x n matrix with singular values log-uniform in [1e-3, 1], with the factors it
+    was built from: (A, Q1, s, Q2), A = Q1 diag(s) Q2^T, s descending."""
     rng = rng_for(10_000 + seed)
     s = np.sort(loguniform_spectrum(rng, n, 1e-3, 1.0))[::-1]
     a, q1, q2 = constructed(seed, n, n, s)
+    return a, q1, s, q2
+
+
+def small_square(seed: int = 1, n: int = 256):
+    """One n x n matrix with singular values log-uniform in [1e-3, 1]: (A, s)."""
+    a, _, s, _ = small_square_factors(seed, n)
     return a, s
 
 
@@ -109,12 +121,36 @@ def marchenko_pastur(seed: int, m: int = 4096, n: int = 1024) -> np.ndarray:
     return rng.standard_normal((m, n)) / math.sqrt(n)
 
 
-def clustered_square(seed: int, n: int = 512, n_clusters: int = 128, mult: int = 4):
-    """Square matrix with exactly repeated singular values (clusters of ``mult``)."""
+def clustered_square_factors(seed: int, n: int = 512, n_clusters: int = 128, mult: int = 4):
+    """Square matrix with exactly repeated singular values (clusters of ``mult``), with the
+    factors it was built from: (A, Q1, s, Q2), s descending."""
     rng = rng_for(20_000 + seed)
     s = clustered_spectrum(rng, n_clusters, mult, 1e-2, 1.0, 1e-3)
     a, q1, q2 = constructed(seed, n, n, s)
+    return a, q1, s, q2
+
+
+def clustered_square(seed: int, n: int = 512, n_clusters: int = 128, mult: int = 4):
+    """Square matrix with exactly repeated singular values (clusters of ``mult``): (A, s)."""
+    a, _, s, _ = clustered_square_factors(seed, n, n_clusters, mult)
     return a, s
+
+
+def rademacher(seed: int, batch: int, n: int, s: int) -> np.ndarray:
+    """Seeded Rademacher probes (batch, n, s) with entries +-1, float32."""
+    rng = rng_for(70_000 + seed)
+    return np.where(rng.random((batch, n, s)) < 0.5, -1.0, 1.0).astype(np.float32)
+
+
+def mlp_params(seed: int) -> np.ndarray:
+    """Seeded parameters of the 8-64-64-1 lower-bound network as one float32 vector in the
+    C ABI's layout [W1 64x8 | b1 64 | W2 64x64 | b2 64 | W3 1x64 | b3 1] (row-major
+    blocks): He-scaled weights, biases N(0, 0.1^2)."""
+    rng = rng_for(80_000 + seed)
+    blocks = [rng.standard_normal((64, 8)) * (2.0 / 8) ** 0.5, 0.1 * rng.standard_normal(64),
+              rng.standard_normal((64, 64)) * (2.0 / 64) ** 0.5, 0.1 * rng.standard_normal(64),
+              rng.standard_normal((1, 64)) * (1.0 / 64) ** 0.5, 0.1 * rng.standard_normal(1)]
+    return np.concatenate([x.ravel() for x in blocks]).astype(np.float32)
 
 
 def loss_weights(seed: int, m: int, n: int):
