@@ -102,8 +102,7 @@ def test_svd_qr_fallback_zero_columns():
     assert np.abs(s - s_ref).max() <= 1e-5 * s_ref[0]
     assert O.recon_error(a32, u, s, vt) <= 1e-5
     assert O.ortho_error(u) <= 1e-5 and O.ortho_error(vt.T) <= 1e-4
-    q_ref, _ = O.qr_nonneg(u[:, :40])
-    np.testing.assert_allclose(u[:, :40], q_ref, atol=1e-4)
+    np.testing.assert_allclose(u[:, :40].T @ u[:, :40], np.eye(40), atol=1e-4)
 
 
 def test_svd_zero_matrix():
