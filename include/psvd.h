@@ -48,7 +48,8 @@ extern "C" {
 /* ---- options ----------------------------------------------------------- */
 #define PSVD_PREC_FP32       0   /* every product FP32-accurate (split hi+lo TF32, "3xTF32") */
 #define PSVD_PREC_MIXED      1   /* TF32 steps -> 3xTF32 polish, switched per matrix from the
-                                    measured orthogonality residual                          */
+                                    measured orthogonality residual; with the learned
+                                    schedule, bounds below PSVD_MIXED_LB_MIN start at 3xTF32 */
 #define PSVD_PREC_MIXED_BF16 2   /* BF16 early steps -> TF32 -> 3xTF32 polish; the BF16
                                     rounding leaves a rotation that the eigenbasis correction
                                     undoes only to first order (reconstruction ~1e-5 at
