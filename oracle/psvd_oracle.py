@@ -46,7 +46,10 @@ the K_eps regularizer uses eps^(1/2) as printed in Algorithm 4 (kreg_mode 0) wit
 the main text's eps^2 as kreg_mode 1 and the exact eps = 0 mask as kreg_mode 2.
 
 Parity status: every function above is pinned by tests under ``tests/`` against
-closed forms, invariants, library routines or finite differences, except the
+closed forms, invariants, library routines or finite differences (the regularized
+branches -- R_eps's eps^(1/2), T_eps's eps^(1/4), K_eps's eps^(1/2) / eps^2 and
+``polar_bwd`` at eps > 0 -- by hand-derived diagonal and 2 x 2 closed forms of
+Algorithm 4 / Algorithm 3 in ``tests/test_oracle_regularized.py``), except the
 exact numbers of Table 3 (parity unpinned: the table matches neither smooth
 regularizer exactly; only its qualitative shape is tested) and the CANS
 iteration counts (parity unpinned: the paper prints none).
