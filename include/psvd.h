@@ -20,9 +20,12 @@
  *  - The library allocates no memory: every call takes a caller-owned device
  *    workspace of at least psvd_*_workspace_bytes(...) bytes, 256-byte aligned.
  *  - All work is enqueued on `stream` (a cudaStream_t passed as void*; NULL =
- *    legacy default stream).  Unless stated otherwise calls are asynchronous: the
- *    return value reports argument and launch errors only, per-matrix outcomes
- *    land in the device-side psvd_info array.
+ *    legacy default stream).  Unless stated otherwise calls are asynchronous: they
+ *    never wait for the GPU, the return value reports argument and launch errors only,
+ *    and per-matrix outcomes land in the device-side psvd_info array.  Iterations
+ *    whose length is decided on the GPU (the polar steps, the learned schedule's
+ *    conservative rerun, the QR fallback) are enqueued for their whole step budget;
+ *    launches that find nothing left to do return at once.
  *  - Calls on the same workspace must not overlap on the GPU.
  */
 #ifndef PSVD_H
@@ -84,9 +87,8 @@ typedef struct psvd_info {
     int   qr_fallback;     /* 1 if U was re-orthogonalized by QR (Algorithm 1's QR fallback) */
     int   sched_fallback;  /* 1 if the learned schedule missed tol and the conservative
                               schedule was rerun                                          */
-    int   prec_fallback;   /* svd_fwd, mixed precision: 1 if the eigenbasis correction
-                              was too large to trust (corr_max above PSVD_MIXED_CORR_MAX)
-                              and the matrix was recomputed on the FP32-accurate path    */
+    int   prec_fallback;   /* svd_fwd, mixed precision: 1 if a check below failed and the
+                              matrix was recomputed on the FP32-accurate path            */
     int   steps_bf16;      /* steps taken in each precision (mixed path)                 */
     int   steps_tf32;
     int   steps_3xtf32;
@@ -94,20 +96,22 @@ typedef struct psvd_info {
     float scale;           /* sqrt(||M||_1 ||M||_inf) of Algorithm 2                     */
     float corr_max;        /* svd_fwd, mixed precision: max |X_ij| of the rotation that
                               the eigenbasis correction applied (0 otherwise)           */
-    float range_resid;     /* svd_fwd, mixed precision, m > n: ||A - W W^T A||_F / ||A||_F,
-                              the part of A outside the computed polar factor's column
-                              space (0 otherwise)                                        */
+    float recon_est;       /* svd_fwd, mixed precision: ||A - U S V^T||_F / ||A||_F of the
+                              mixed result, estimated from 8 Rademacher probe vectors
+                              (Hutchinson's estimator, float-float sums; 0 otherwise)   */
 } psvd_info;
 
 /* Mixed-precision svd_fwd keeps a matrix's BF16/TF32 result only while both checks
  * hold, and recomputes it on the FP32-accurate path otherwise (prec_fallback = 1):
- *  - corr_max <= PSVD_MIXED_CORR_MAX: the eigenbasis correction is first order, its
- *    error grows like corr_max^2;
- *  - range_resid <= PSVD_MIXED_RANGE_MAX: the polynomial steps multiply X on the right
- *    and never repair its column space, so for m > n the rounding of the low-precision
- *    steps leaves part of A outside it, and that part is missing from U S V^T. */
+ *  - corr_max <= PSVD_MIXED_CORR_MAX: the eigenbasis correction is first order, and
+ *    rotations this large leave it outside its range of validity;
+ *  - recon_est <= PSVD_MIXED_RECON_MAX, half the FP32 reconstruction gate of 1e-5: this
+ *    sees the dense second-order error of the correction (whose largest entry stays
+ *    small while its norm grows like sqrt(n) times it -- BF16 steps at n = 4096), and,
+ *    for m > n, the part of A that the low-precision steps left outside the polar
+ *    factor's column space (the steps multiply X on the right and never repair it). */
 #define PSVD_MIXED_CORR_MAX 2e-3
-#define PSVD_MIXED_RANGE_MAX 5e-6
+#define PSVD_MIXED_RECON_MAX 5e-6
 
 /* PSVD_PREC_MIXED with the learned schedule: a matrix whose lower bound (opts.lower_bound,
  * in units of X0 = M / sqrt(||M||_1 ||M||_inf)) is below PSVD_MIXED_LB_MIN starts on the
@@ -135,17 +139,20 @@ int psvd_polar_fwd(const float *A, float *W, float *H, int64_t batch, int64_t m,
                    void *stream);
 
 /* psvd_polar_fwd_noalloc -- psvd_polar_fwd for callers that cannot allocate device
- *   memory (no counterpart in the paper): code that runs while a CUDA graph is being
- *   captured, in a real-time loop that forbids allocator calls, or under a memory
- *   manager that owns every cudaMalloc.  Same arguments and results as psvd_polar_fwd
- *   minus the workspace: the scratch is a fixed device array inside the library, of
+ *   memory (no counterpart in the paper): a real-time loop whose allocator calls are
+ *   forbidden because they can block or fragment memory, an embedding that hands all
+ *   device memory to its own memory manager, or a plugin that is given only its input
+ *   and output buffers.  Same arguments, checks and results as psvd_polar_fwd minus
+ *   the workspace: the scratch is a fixed device array inside the library, of
  *   psvd_polar_noalloc_capacity() bytes (64 MiB), held on every GPU that loads the
  *   library until the process exits.  A problem whose psvd_polar_workspace_bytes exceeds
- *   it is rejected with PSVD_ERR_WORKSPACE (psvd_last_error says so) before any work.
- *   The first call on each device looks up the array's device address with the device
- *   current; make that first call before capturing a stream.  Every call shares the one
- *   array (each call clears what it needs), so calls that overlap on the GPU -- other
- *   streams, other host threads -- race; serialize them.  Calls no cudaMalloc/cudaFree. */
+ *   it is rejected with PSVD_ERR_WORKSPACE before any work (psvd_last_error gives the
+ *   needed and available bytes).  The first call on each device (and the first after a
+ *   cudaDeviceReset) looks up the array's device address with that device current; make
+ *   it before any stream capture.  Every call shares the one array and leaves its
+ *   contents behind (each call clears what it needs), so calls that overlap on the GPU
+ *   -- other streams, other host threads -- race; serialize them.  Calls no
+ *   cudaMalloc/cudaFree and no allocating library routine. */
 int psvd_polar_fwd_noalloc(const float *A, float *W, float *H, int64_t batch, int64_t m, int64_t n,
                            const psvd_opts *opts, psvd_info *info, void *stream);
 size_t psvd_polar_noalloc_capacity(void);
@@ -153,7 +160,9 @@ size_t psvd_polar_noalloc_capacity(void);
 /* psvd_svd_fwd -- thin SVD M = U Sigma V^T by Algorithm 1.
  *   U: batch x m x n, S: batch x n (descending, >= 0 up to rounding), VT: batch x n x n
  *   (rows are right singular vectors; each V column's largest-|.| entry is positive).
- *   This call synchronizes `stream` once (it reads back the QR-fallback flags). */
+ *   With PSVD_PREC_FP32 the call is asynchronous.  In the mixed modes it synchronizes
+ *   `stream` exactly once, after the mixed pass, to read which matrices failed the
+ *   checks above; those are recomputed on the FP32-accurate path in the same call. */
 int psvd_svd_fwd(const float *A, float *U, float *S, float *VT, int64_t batch, int64_t m,
                  int64_t n, const psvd_opts *opts, void *ws, size_t ws_bytes,
                  psvd_info *info, void *stream);

@@ -39,11 +39,11 @@ class Opts(ctypes.Structure):
 
 
 INFO_FIELDS = ["status", "iters", "qr_fallback", "sched_fallback", "prec_fallback", "steps_bf16", "steps_tf32",
-               "steps_3xtf32", "ortho_resid", "scale", "corr_max", "range_resid"]
+               "steps_3xtf32", "ortho_resid", "scale", "corr_max", "recon_est"]
 INFO_INTS = 8   # the first 8 fields are int32, the rest float32
 INFO_WORDS = len(INFO_FIELDS)
 MIXED_CORR_MAX = 2e-3    # PSVD_MIXED_CORR_MAX of psvd.h
-MIXED_RANGE_MAX = 5e-6   # PSVD_MIXED_RANGE_MAX of psvd.h
+MIXED_RECON_MAX = 5e-6   # PSVD_MIXED_RECON_MAX of psvd.h
 MIXED_LB_MIN = 5e-5      # PSVD_MIXED_LB_MIN of psvd.h
 
 

@@ -70,6 +70,8 @@ struct GemmShape {
     int prec_uniform;       // used when prec == nullptr
     const int *prec;        // [batch] per-matrix precision, or nullptr
     const int *skip;        // [batch] nonzero = matrix finished, its tiles are skipped (or nullptr)
+    const int *gate;        // nullptr, or a device counter: 0 = nothing left to do, the whole launch
+                            // returns at once (written by an earlier kernel on the same stream)
     unsigned *err;          // device error word
 };
 
@@ -214,6 +216,9 @@ PSVD_DEV bool mma_tile_x3(MmaRing &r, int nkb, uint32_t tmem, uint64_t *acc_full
 template <class Epi>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 gemm_tn_kernel(const __grid_constant__ GemmMaps maps, const GemmShape shp, Epi epi) {
+    // A gated launch with nothing left to do returns before any allocation (uniform: every
+    // thread reads the same word, final since the kernel that wrote it has completed).
+    if (shp.gate && *shp.gate == 0) return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + kRingBytes);

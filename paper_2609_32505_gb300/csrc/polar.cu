@@ -322,7 +322,7 @@ __global__ void polar_info_kernel(int B, const int *status, const int *fin, cons
     r.sched_fallback = fallback[b];
     r.prec_fallback = 0;
     r.corr_max = 0.f;
-    r.range_resid = 0.f;
+    r.recon_est = 0.f;
     r.steps_bf16 = steps[b];
     r.steps_tf32 = steps[B + b];
     r.steps_3xtf32 = steps[2 * B + b];
@@ -332,7 +332,12 @@ __global__ void polar_info_kernel(int B, const int *status, const int *fin, cons
 }
 
 // ------------------------------------------------------------ host driver
-static int launch_step(PolarWS &w, int k, bool apply, double tol, bool learned, float *fres, cudaStream_t st) {
+// Step k: Gram (with the polynomial and residual epilogue), decision, apply.  The Gram
+// launch is gated on `gram_gate` (the count of matrices still iterating; nullptr = always
+// run) and the apply launch on this step's own count, so once every matrix has finished
+// the remaining launches of the budget return at once.
+static int launch_step(PolarWS &w, int k, bool apply, double tol, bool learned, float *fres, const int *gram_gate,
+                       cudaStream_t st) {
     const int B = w.B, m = w.m, n = w.n;
     const int par = k & 1, npar = (k + 1) & 1;
     // Gram: A = B = X^T (n x m, K = m), upper-triangle tiles
@@ -345,6 +350,7 @@ static int launch_step(PolarWS &w, int k, bool apply, double tol, bool learned, 
         s.M = n; s.N = n; s.K = m; s.sym = 1;
         s.prec = w.prec + (long long)k * B;
         s.skip = w.done;
+        s.gate = gram_gate;
         s.err = w.err;
         EpiGram e;
         e.n = n; e.B = B;
@@ -376,6 +382,7 @@ static int launch_step(PolarWS &w, int k, bool apply, double tol, bool learned, 
         s.M = m; s.N = n; s.K = n;
         s.prec = w.prec + (long long)k * B;
         s.skip = w.done;
+        s.gate = w.notdone + k;          // matrices still iterating after this step's decision
         s.err = w.err;
         EpiApply e;
         e.m = m; e.n = n; e.B = B;
@@ -390,37 +397,17 @@ static int launch_step(PolarWS &w, int k, bool apply, double tol, bool learned, 
     return PSVD_OK;
 }
 
-static int read_int(const int *dptr, cudaStream_t st, int *out) {
-    if (cudaMemcpyAsync(out, dptr, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return PSVD_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return PSVD_ERR_CUDA;
-    return PSVD_OK;
-}
-
-// Runs steps 0..kcap until every matrix is done; `predicted` steps are launched
-// before the first host check, then 3 at a time.
-static int run_iteration(PolarWS &w, int predicted, double tol, bool learned, float *fres, cudaStream_t st) {
-    int k = 0;
-    int until = std::min(w.kcap, std::max(1, predicted));
-    while (true) {
-        for (; k <= until; ++k) {
-            int rc = launch_step(w, k, k < w.kcap, tol, learned, fres, st);
-            if (rc) return rc;
-        }
-        if (k > w.kcap) break;
-        int nd = 0;
-        if (int rc = read_int(w.notdone + (k - 1), st, &nd)) return rc;
-        if (nd == 0) break;
-        until = std::min(w.kcap, k + 2);
+// Launches steps 0..kmax (kmax <= kcap) with no host synchronization: the decision kernel
+// of step k counts the matrices still iterating in notdone[k], and the launches after the
+// last matrix has finished find their gate at 0 and return at once.  `first_gate` gates
+// the Gram launch of step 0 (nullptr: always run).
+static int run_iteration(PolarWS &w, int kmax, double tol, bool learned, float *fres, const int *first_gate,
+                         cudaStream_t st) {
+    for (int k = 0; k <= kmax; ++k) {
+        const int *gate = k == 0 ? first_gate : w.notdone + (k - 1);
+        if (int rc = launch_step(w, k, k < w.kcap, tol, learned, fres, gate, st)) return rc;
     }
     return PSVD_OK;
-}
-
-// Predicted number of steps for the conservative schedule to reach width tol/2
-// for spectra in [t, 1] (used only to size the first launch batch).
-static int predict_steps(const std::vector<Cubic> &sched, double tol) {
-    for (size_t k = 0; k < sched.size(); ++k)
-        if (sched[k].e <= 0.5 * tol) return (int)k + 1;
-    return (int)sched.size();
 }
 
 __global__ void fallback_reset_kernel(int B, int prec0, const int *fallback, int *done, int *prec, int *count) {
@@ -488,28 +475,31 @@ int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &
         if (prepare_operand(A, n, (long long)m * n, B, m, n, true, 1.f, nullptr, at, st)) return PSVD_ERR_CUDA;
     }
     if (cudaGetLastError() != cudaSuccess) return PSVD_ERR_CUDA;
-    const int predicted = o.schedule == PSVD_SCHED_CANS ? predict_steps(sched, o.tol) : 12;
-    if (int rc = run_iteration(w, predicted, o.tol, learned, w.fres, st)) return rc;
+    // Host-side bound on the steps any matrix can take: the cap for the conservative and
+    // Newton-Schulz schedules; for the learned one, the largest budget a lower bound can
+    // produce (the bound is clamped to >= 1e-12 on the device) or the caller's budget.
+    int kmax = w.kcap;
+    if (learned) kmax = std::min(w.kcap, o.budget > 0 ? o.budget : greedy_steps_to(1e-12, 0.5 * o.tol, w.kcap + 1) + 5);
+    if (int rc = run_iteration(w, kmax, o.tol, learned, w.fres, nullptr, st)) return rc;
     if (learned) {
-        // matrices whose learned schedule missed tol within budget: conservative rerun
+        // Matrices whose learned schedule missed tol within budget are rerun from X0 with the
+        // conservative schedule.  Nothing is read back: the rerun's steps are launched for the
+        // whole budget, gated on the number of rerun matrices (misc[0]) and then on the
+        // per-step counts, so without a fallback every one of them returns at once.
         fallback_reset_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, prec0, w.fallback, w.done, w.prec, w.misc);
         count_launch(1);
-        int nfb = 0;
-        if (int rc = read_int(w.misc, st, &nfb)) return rc;
-        if (nfb > 0) {
-            CoefTable ct;
-            memset(&ct, 0, sizeof(ct));
-            ct.len = (int)cons.size();
-            for (int i = 0; i < ct.len; ++i) { ct.c1[i] = (float)cons[i].c1; ct.c3[i] = (float)cons[i].c3; }
-            schedule_fill_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, w.kcap + 1, ct, nullptr, 0, o.tol, 0,
-                                                                  w.fallback, w.coef, w.budget, 0, w.prec);
-            count_launch(1);
-            if (cudaMemsetAsync(w.res, 0, sizeof(double) * (size_t)(w.kcap + 2) * B, st) ||
-                cudaMemsetAsync(w.notdone, 0, sizeof(int) * (size_t)(w.kcap + 2), st))
-                return PSVD_ERR_CUDA;
-            if (int rc = prepare_x0(A, w, st, w.done)) return rc;
-            if (int rc = run_iteration(w, predict_steps(cons, o.tol), o.tol, false, w.fres, st)) return rc;
-        }
+        CoefTable ct;
+        memset(&ct, 0, sizeof(ct));
+        ct.len = (int)cons.size();
+        for (int i = 0; i < ct.len; ++i) { ct.c1[i] = (float)cons[i].c1; ct.c3[i] = (float)cons[i].c3; }
+        schedule_fill_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, w.kcap + 1, ct, nullptr, 0, o.tol, 0,
+                                                              w.fallback, w.coef, w.budget, 0, w.prec);
+        count_launch(1);
+        if (cudaMemsetAsync(w.res, 0, sizeof(double) * (size_t)(w.kcap + 2) * B, st) ||
+            cudaMemsetAsync(w.notdone, 0, sizeof(int) * (size_t)(w.kcap + 2), st))
+            return PSVD_ERR_CUDA;
+        if (int rc = prepare_x0(A, w, st, w.done)) return rc;
+        if (int rc = run_iteration(w, w.kcap, o.tol, false, w.fres, w.misc, st)) return rc;
         set_all_done_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, w.done);
         count_launch(1);
     }
@@ -588,7 +578,8 @@ extern "C" int psvd_polar_fwd(const float *A, float *W, float *H, int64_t batch,
 // Scratch for psvd_polar_fwd_noalloc: a fixed device array in this file, present on every
 // GPU that loads the library until the process exits.  Host code must not pass the
 // symbol itself to a kernel (on the host it names a stand-in object); its device address
-// is looked up once per device with cudaGetSymbolAddress while that device is current.
+// is looked up with cudaGetSymbolAddress once per device, with that device current, and
+// again after the device's context has changed (cudaDeviceReset reloads the module).
 static constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -598,6 +589,7 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void *g_noalloc_ptr[kMaxDevices] = {};
+unsigned long long g_noalloc_ctx[kMaxDevices] = {};
 }  // namespace
 
 extern "C" size_t psvd_polar_noalloc_capacity(void) { return kNoAllocScratchBytes; }
@@ -605,25 +597,29 @@ extern "C" size_t psvd_polar_noalloc_capacity(void) { return kNoAllocScratchByte
 extern "C" int psvd_polar_fwd_noalloc(const float *A, float *W, float *H, int64_t batch, int64_t m, int64_t n,
                                       const psvd_opts *opts, psvd_info *info, void *stream) {
     psvd_opts o = resolve_opts(opts);
-    if (!A || !W || batch <= 0 || n <= 0 || m < n || batch > 65535 || !opts_ok(o)) return PSVD_ERR_ARG;
+    // the same argument checks as psvd_polar_fwd
+    if (!A || !W || batch <= 0 || n <= 0 || m < n || batch > 65535 || m > (1 << 28) / 1 || !opts_ok(o))
+        return PSVD_ERR_ARG;
     if ((long long)m * n > (1LL << 31)) return PSVD_ERR_ARG;
     if (int e = check_device()) return e;
     const size_t need = psvd_polar_workspace_bytes(batch, m, n, &o);
-    if (need > kNoAllocScratchBytes) {
-        cuda_fail(cudaErrorInvalidValue, "psvd_polar_fwd_noalloc: problem needs more scratch than the static 64 MiB",
-                  (int)(need >> 20));
-        return PSVD_ERR_WORKSPACE;
-    }
+    if (need > kNoAllocScratchBytes)
+        return fail_msg(PSVD_ERR_WORKSPACE,
+                        "psvd_polar_fwd_noalloc: a %lld x %lld x %lld problem needs %zu bytes of scratch, "
+                        "the static array holds %zu", (long long)batch, (long long)m, (long long)n, need,
+                        kNoAllocScratchBytes);
     int dev = 0;
     PSVD_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return PSVD_ERR_ARG;
+    const unsigned long long ctx = current_context_id();
     void *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
+        if (!g_noalloc_ptr[dev] || g_noalloc_ctx[dev] != ctx) {
             void *p = nullptr;
             PSVD_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
             g_noalloc_ptr[dev] = p;
+            g_noalloc_ctx[dev] = ctx;
         }
         scratch = g_noalloc_ptr[dev];
     }

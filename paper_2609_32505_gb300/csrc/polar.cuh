@@ -85,8 +85,9 @@ inline int polar_kcap(const psvd_opts &o) { return o.max_iter + (o.schedule == P
 // Runs the iteration of Algorithm 1 (normalize, schedule, iterate) for all matrices, then
 // writes W (user layout, may be null) and leaves W^T split in XThi[0]/XTlo[0] and W
 // split in Xhi[0]/Xlo[0].  If `want_h`, also computes Hsym = (W^T M)_sym (FP64
-// averaging) and copies it to H_out (may be null).  Synchronizes the stream a few
-// times to decide how many steps to launch.  Fills info (device, may be null).
+// averaging) and copies it to H_out (may be null).  Never synchronizes: the step budget is
+// launched whole and finished matrices are skipped on the device.  Fills info (device,
+// may be null).
 int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &ws, const psvd_opts &o,
                   psvd_info *info, cudaStream_t st);
 

@@ -45,6 +45,11 @@ inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? PSVD_OK : PSVD
 // Records where a CUDA call failed (readable through psvd_last_error) and returns
 // PSVD_ERR_CUDA.
 int cuda_fail(cudaError_t e, const char *file, int line);
+// Records a free-form message for psvd_last_error (printf-style) and returns `status`.
+int fail_msg(int status, const char *fmt, ...);
+// Unique ID of the calling thread's current CUDA context (cuCtxGetId through the driver
+// entry point; distinct for a context created after cudaDeviceReset), 0 if unavailable.
+unsigned long long current_context_id();
 #define PSVD_TRY(expr)                                                        \
     do {                                                                      \
         cudaError_t _psvd_e = (expr);                                         \

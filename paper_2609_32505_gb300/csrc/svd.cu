@@ -189,48 +189,102 @@ __global__ void corr_x_kernel(const float *Kt, const float *S, int n, float *X, 
     if (((threadIdx.y * 16 + threadIdx.x) & 31) == 0 && bits) atomicMax(&xmax[b], bits);
 }
 
-// ||A||_F^2 and ||A - W Hhat||_F^2 per matrix (Hhat = W^T A): the part of A outside the
-// column space of W.  Nothing is stored.
-struct EpiRange {
-    int m, n;
-    const float *A;
-    double *sums;     // [B][2]
-    struct Acc { double a, r; };
-    PSVD_DEV void begin(Acc &s) const { s.a = 0.0; s.r = 0.0; }
-    PSVD_DEV void chunk(Acc &s, int b, int r, int c0, int, int, float (&v)[16]) const {
-        if (r >= m) return;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int c = c0 + i;
-            if (c >= n) break;
-            const float a = A[(long long)b * m * n + (long long)r * n + c];
-            const float d = a - v[i];
-            s.a += (double)a * a;
-            s.r += (double)d * d;
-        }
-    }
-    PSVD_DEV void finish(Acc &s, int b, int, int) const {
-        const double a = warp_sum(s.a), r = warp_sum(s.r);
-        if ((threadIdx.x & 31) == 0) {
-            if (a != 0.0) atomicAdd(&sums[2 * b], a);
-            if (r != 0.0) atomicAdd(&sums[2 * b + 1], r);
-        }
-    }
-};
+// ------------------------------------------------------------ reconstruction check
+// ||A - U Sigma V^T||_F^2 = E_z ||(A - U Sigma V^T) z||^2 for Rademacher z (Hutchinson's
+// estimator); kProbes probes give an estimate whose relative spread is about
+// sqrt(2 / (kProbes * r_eff)), r_eff the effective rank of the error (high for the dense
+// second-order error the mixed path leaves).  Sums are float-float, so the difference
+// A z - U (Sigma V^T z) keeps ~1e-14 relative accuracy where the error is ~1e-6.
+constexpr int kProbes = 8;
 
-// Matrices whose correction rotation or range residual is too large to trust are
-// flagged for the FP32-accurate rerun; records both in info.
-__global__ void mixed_flag_kernel(const unsigned *xmax, const double *rsums, int B, float corr_limit,
-                                  float range_limit, int *mflag, int *count, psvd_info *info) {
+// Signs of the kProbes probes at column j: bits of a 32-bit integer hash of j.
+PSVD_DEV unsigned probe_hash(int j) {
+    unsigned h = (unsigned)j * 0x9E3779B1u + 0x632BE5ABu;
+    h ^= h >> 16; h *= 0x85EBCA6Bu; h ^= h >> 13; h *= 0xC2B2AE35u; h ^= h >> 16;
+    return h;
+}
+PSVD_DEV float probe_sign(unsigned h, int p) { return (h >> p) & 1u ? -1.f : 1.f; }
+
+// Y[b][p][i] = sigma_i (V^T z_p)_i: one warp per row i of V^T.
+__global__ void probe_vt_kernel(const float *VT, const float *S, int n, float *Y) {
+    const int b = blockIdx.y;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const float *v = VT + ((long long)b * n + i) * n;
+    ff acc[kProbes];
+#pragma unroll
+    for (int p = 0; p < kProbes; ++p) acc[p] = ff_zero();
+    for (int j = lane; j < n; j += 32) {
+        const float x = v[j];
+        const unsigned h = probe_hash(j);
+#pragma unroll
+        for (int p = 0; p < kProbes; ++p) acc[p] = ff_add(acc[p], ff{probe_sign(h, p) * x, 0.f});
+    }
+#pragma unroll
+    for (int p = 0; p < kProbes; ++p) acc[p] = warp_sum(acc[p]);
+    if (lane == 0) {
+        const float sg = S[(long long)b * n + i];
+#pragma unroll
+        for (int p = 0; p < kProbes; ++p) Y[((long long)b * kProbes + p) * n + i] = sg * __fadd_rn(acc[p].hi, acc[p].lo);
+    }
+}
+
+// Per row r: res_p = A[r, :] z_p - U[r, :] Y[p, :]; sums[b] += (||A[r, :]||^2, sum_p res_p^2),
+// one warp per row, reduced over the block before one atomic pair.
+__global__ void __launch_bounds__(256) probe_resid_kernel(const float *A, const float *U, const float *Y, int m,
+                                                          int n, double *sums) {
+    __shared__ double red[2][8];
+    const int b = blockIdx.y, wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * 8 + wp;
+    double a2 = 0.0, rs = 0.0;
+    if (r < m) {
+        const float *a = A + ((long long)b * m + r) * n, *u = U + ((long long)b * m + r) * n;
+        const float *y = Y + (long long)b * kProbes * n;
+        ff acc[kProbes];
+#pragma unroll
+        for (int p = 0; p < kProbes; ++p) acc[p] = ff_zero();
+        ff an = ff_zero();
+        for (int j = lane; j < n; j += 32) {
+            const float x = a[j], uu = u[j];
+            const unsigned h = probe_hash(j);
+            an = ff_fma(an, x, x);
+#pragma unroll
+            for (int p = 0; p < kProbes; ++p) {
+                acc[p] = ff_add(acc[p], ff{probe_sign(h, p) * x, 0.f});
+                acc[p] = ff_fma(acc[p], -uu, y[(long long)p * n + j]);
+            }
+        }
+        an = warp_sum(an);
+        a2 = (double)an.hi + (double)an.lo;
+#pragma unroll
+        for (int p = 0; p < kProbes; ++p) {
+            const ff t = warp_sum(acc[p]);
+            const double d = (double)t.hi + (double)t.lo;
+            rs += d * d;
+        }
+    }
+    if (lane == 0) { red[0][wp] = a2; red[1][wp] = rs; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sr = 0.0;
+        for (int w = 0; w < 8; ++w) { sa += red[0][w]; sr += red[1][w]; }
+        if (sa != 0.0) atomicAdd(&sums[2 * b], sa);
+        if (sr != 0.0) atomicAdd(&sums[2 * b + 1], sr);
+    }
+}
+
+// Matrices whose correction rotation or estimated reconstruction error is too large to
+// trust are flagged for the FP32-accurate rerun; records both in info.
+__global__ void mixed_flag_kernel(const unsigned *xmax, const double *sums, int B, float corr_limit,
+                                  float recon_limit, int *mflag, int *count, psvd_info *info) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     const float x = __uint_as_float(xmax[b]);
-    float rr = 0.f;
-    if (rsums) rr = rsums[2 * b] > 0.0 ? (float)sqrt(rsums[2 * b + 1] / rsums[2 * b]) : 0.f;
-    const int f = !(x <= corr_limit) || !(rr <= range_limit);
+    const float est = sums[2 * b] > 0.0 ? (float)sqrt(sums[2 * b + 1] / (kProbes * sums[2 * b])) : 0.f;
+    const int f = !(x <= corr_limit) || !(est <= recon_limit);
     mflag[b] = f;
     if (f) atomicAdd(count, 1);
-    if (info) { info[b].corr_max = x; info[b].range_resid = rr; }
+    if (info) { info[b].corr_max = x; info[b].recon_est = est; }
 }
 
 // Results of the FP32-accurate rerun replace the flagged matrices' records.
@@ -240,7 +294,7 @@ __global__ void info_scatter_kernel(psvd_info *info, const psvd_info *infoc, con
     psvd_info r = infoc[j];
     r.prec_fallback = 1;
     r.corr_max = info[idx[j]].corr_max;
-    r.range_resid = info[idx[j]].range_resid;
+    r.recon_est = info[idx[j]].recon_est;
     info[idx[j]] = r;
 }
 
@@ -331,9 +385,9 @@ struct SvdWS {
     float *X = nullptr, *Xneg = nullptr, *X2 = nullptr, *F = nullptr, *Ft = nullptr, *VEt = nullptr;
     unsigned *xmax = nullptr;
     int *mflag = nullptr;
-    double *rsums = nullptr;     // [B][2] range check sums (m > n)
+    double *rsums = nullptr;     // [B][2] reconstruction-check sums
+    float *Yp = nullptr;         // [B][kProbes][n] sigma (V^T z) for the check
     bool mixed = false;
-    int n_mixed_fallback = 0;    // set by svd_forward
 
     template <class C>
     void carve(C &cv, int B, int m, int n, const psvd_opts &o) {
@@ -368,6 +422,7 @@ struct SvdWS {
             xmax = cv.template take<unsigned>(B64);
             mflag = cv.template take<int>(B64);
             rsums = cv.template take<double>(B64 * 2);
+            Yp = cv.template take<float>(B64 * kProbes * n);
         }
     }
 };
@@ -410,18 +465,6 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
         SplitOut vo;
         vo.hi = w.Vhi; vo.lo = w.Vlo; vo.ld = ld; vo.bstride = nn;
         if (prepare_operand(vthi, ld, nn, B, n, n, true, 1.f, nullptr, vo, st)) return PSVD_ERR_CUDA;
-        if (m > n) {
-            // range check: W Hhat against A, with Hhat^T split into Khi/Klo for the B operand
-            SplitOut ho;
-            ho.hi = w.Khi; ho.lo = w.Klo; ho.ld = ld; ho.bstride = nn;
-            if (prepare_operand(p.Hraw, n, (long long)n * n, B, n, n, true, 1.f, nullptr, ho, st)) return PSVD_ERR_CUDA;
-            if (cudaMemsetAsync(w.rsums, 0, sizeof(double) * 2 * (size_t)B, st)) return PSVD_ERR_CUDA;
-            EpiRange er;
-            er.m = m; er.n = n; er.A = A; er.sums = w.rsums;
-            if (int rc = gemm3(p.Xhi[0], p.Xlo[0], m, n, p.ldn, (long long)m * p.ldn, w.Khi, w.Klo, n, ld, nn, B,
-                               PREC_TF32X3, er, p.err, st))
-                return rc;
-        }
         skewT_kernel<<<g16, b16, 0, st>>>(p.Hraw, n, w.Khi, w.Klo, ld);     // K^T, K = skew(Hhat)
         count_launch(1);
         // T1 = V^T K   (B operand B[j][k] = K[k][j] = K^T[j][k])
@@ -435,11 +478,8 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
         if (int rc = gemm3(w.T1hi, w.T1lo, n, n, ld, nn, vthi, vtlo, n, ld, nn, B, PREC_TF32X3, e2, p.err, st)) return rc;
         if (cudaMemsetAsync(w.xmax, 0, sizeof(unsigned) * (size_t)B, st)) return PSVD_ERR_CUDA;
         corr_x_kernel<<<g16, b16, 0, st>>>(w.Kt, w.S, n, w.X, w.Ft, w.Xneg, ld, w.xmax);   // X_lo in Ft
-        mixed_flag_kernel<<<(B + 127) / 128, 128, 0, st>>>(w.xmax, m > n ? w.rsums : nullptr, B,
-                                                           (float)PSVD_MIXED_CORR_MAX, (float)PSVD_MIXED_RANGE_MAX,
-                                                           w.mflag, w.any + 1, info);
         sigma_refresh_kernel<<<dim3((n + 7) / 8, B), 256, 0, st>>>(w.X, w.S, n, ld, Sout, nullptr);
-        count_launch(3);
+        count_launch(2);
         // X^2 = X X   (B operand B[j][k] = X[k][j] = -X[j][k])
         EpiStore e3 = epi_store_plain(w.X2, n, (long long)n * n, n, n);
         if (int rc = gemm3(w.X, nullptr, n, n, ld, nn, w.Xneg, nullptr, n, ld, nn, B, PREC_TF32, e3, p.err, st)) return rc;
@@ -477,12 +517,9 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
     }
     qr_flag_kernel<<<B, 256, 0, st>>>(w.colss, n, o.eps_qr, w.flag, w.any);
     count_launch(1);
-    int counts[2] = {0, 0};      // QR fallbacks, mixed-precision fallbacks
-    if (cudaMemcpyAsync(counts, w.any, sizeof(counts), cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
-        return PSVD_ERR_CUDA;
-    w.n_mixed_fallback = w.mixed ? counts[1] : 0;
-    const int nflag = counts[0];
-    if (nflag > 0) {
+    // QR fallback (Appendix A.2), decided on the device: the kernels run for the flagged
+    // matrices only and return at once when none is flagged, so nothing is read back.
+    {
         QrParams q;
         q.U = U; q.UT = w.UT; q.tau = w.qtau; q.beta = w.qbeta; q.flag = w.flag; q.bar = w.qbar; q.err = p.err;
         q.B = B; q.m = m; q.n = n;
@@ -501,6 +538,16 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
             info_qr_kernel<<<(B + 127) / 128, 128, 0, st>>>(info, w.flag, B);
             count_launch(1);
         }
+    }
+    if (w.mixed) {
+        // the mixed result's reconstruction error, estimated from kProbes probes of the final
+        // factors, and the decision to keep it or recompute the matrix on the FP32 path
+        PSVD_TRY(cudaMemsetAsync(w.rsums, 0, sizeof(double) * 2 * (size_t)B, st));
+        probe_vt_kernel<<<dim3((n + 7) / 8, B), 256, 0, st>>>(VT, Sout, n, w.Yp);
+        probe_resid_kernel<<<dim3((m + 7) / 8, B), 256, 0, st>>>(A, U, w.Yp, m, n, w.rsums);
+        mixed_flag_kernel<<<(B + 127) / 128, 128, 0, st>>>(w.xmax, w.rsums, B, (float)PSVD_MIXED_CORR_MAX,
+                                                           (float)PSVD_MIXED_RECON_MAX, w.mflag, w.any + 1, info);
+        count_launch(3);
     }
     return cudaGetLastError() == cudaSuccess ? PSVD_OK : PSVD_ERR_CUDA;
 }
@@ -614,7 +661,8 @@ extern "C" int psvd_svd_fwd(const float *A, float *U, float *S, float *VT, int64
     if (cv.overflow) return PSVD_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     PSVD_TRY_RC(svd_forward(A, U, S, VT, w, o, info, st));
-    if (w.n_mixed_fallback > 0)
-        return mixed_fallback(A, U, S, VT, (int)batch, (int)m, (int)n, w, o, ws, ws_bytes, info, st);
+    // mixed precision: the one host synchronization of this call (reads which matrices the
+    // checks flagged for the FP32-accurate rerun)
+    if (w.mixed) return mixed_fallback(A, U, S, VT, (int)batch, (int)m, (int)n, w, o, ws, ws_bytes, info, st);
     return PSVD_OK;
 }

@@ -98,7 +98,7 @@ def test_python_mirrors_of_header_constants():
     assert (P.SCHED_CANS, P.SCHED_LEARNED, P.SCHED_NS) == (d["PSVD_SCHED_CANS"], d["PSVD_SCHED_LEARNED"],
                                                            d["PSVD_SCHED_NS"])
     assert P.MIXED_CORR_MAX == d["PSVD_MIXED_CORR_MAX"]
-    assert P.MIXED_RANGE_MAX == d["PSVD_MIXED_RANGE_MAX"]
+    assert P.MIXED_RECON_MAX == d["PSVD_MIXED_RECON_MAX"]
     assert P.MIXED_LB_MIN == d["PSVD_MIXED_LB_MIN"]
     assert [name for _, name in fields] == P.INFO_FIELDS
     assert [t for t, _ in fields] == ["int"] * P.INFO_INTS + ["float"] * (P.INFO_WORDS - P.INFO_INTS)

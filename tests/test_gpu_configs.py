@@ -126,3 +126,30 @@ def test_config_learned_schedule_families():
     steps_c = np.mean([info_c[b]["iters"] for b in ok])
     steps_l = np.mean([info_l[b]["iters"] for b in ok])
     assert steps_l < steps_c, (steps_l, steps_c)
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_config_headline_square_mixed_modes(precision):
+    # The benchmark's matrix: 4096 x 4096, A = Q1 diag(s) Q2^T with s_i = 10^((n-i)/(n-1))
+    # (kappa = 10, the square setting of Section 4.1 / Tables 1-2), in both mixed modes.
+    # Whether the mixed result is kept or recomputed on the FP32-accurate path, the returned
+    # factors must meet the four gates, and the record must say which happened.
+    import paper_2609_32505_gb300 as P
+    n = 4096
+    s0 = W.kappa_spectrum(n, 10.0)
+    A = W.torch_constructed(1000, n, n, s0, device="cuda")
+    U, S, VT, info = P.svd_fwd(A, P.make_opts(precision=precision), return_info=True)
+    torch.cuda.synchronize()
+    i = info[0]
+    assert i["status"] == 0
+    bad = not (i["corr_max"] <= P.MIXED_CORR_MAX) or not (i["recon_est"] <= P.MIXED_RECON_MAX)
+    assert i["prec_fallback"] == int(bad)
+    rec, ou, ov = _props(A, U, S, VT)[0]
+    # Weyl: the FP32 rounding E of the FP64 product moves each sigma by <= ||E||_2 <= u ||A||_F
+    weyl = 2.0 ** -24 * float(torch.linalg.matrix_norm(A[0].double()))
+    sig = float((S[0].double().cpu() - torch.from_numpy(s0)).abs().max())
+    assert sig <= 1e-5 * s0[0] + weyl
+    assert rec <= 1e-5 and ou <= 1e-4 and ov <= 1e-4, (rec, ou, ov, i)
+    if i["prec_fallback"] == 0:
+        # the kept mixed result: the estimate within a factor 3 of the measured error
+        assert rec / 3.0 <= i["recon_est"] <= 3.0 * rec + 1e-7, (rec, i["recon_est"])

@@ -40,10 +40,15 @@ def test_polar_parity(m, n, kappa, precision):
     else:
         # BF16/TF32 steps rotate X inside low-sigma subspaces (invisible to the
         # orthogonality residual, kept by later steps); H = (W^T A)_sym is still an
-        # FP32-accurate product, so A = W H holds to the low-precision level
+        # FP32-accurate product, so A - W H = W skew(W^T A) is that rotation's footprint.
+        # Bound: the paper's all-TF32 variant reaches ||A - U S V^T||_F / ||A||_F <= 1.2e-3
+        # at every kappa of Table 1; here only the polynomial steps are low precision, so
+        # TF32 stays within 2e-3, and BF16 (unit roundoff 2^-9, four times TF32's 2^-11)
+        # within four times that.
         low = "steps_bf16" if precision == 2 else "steps_tf32"
         assert info[0][low] > 0 and info[0]["steps_3xtf32"] > 0
-        assert np.linalg.norm(a32 - w @ h) / np.linalg.norm(a32) < 5e-2
+        bound = 2e-3 if precision == 1 else 8e-3
+        assert np.linalg.norm(a32 - w @ h) / np.linalg.norm(a32) < bound
 
 
 def test_polar_batch_and_schedules():

@@ -33,7 +33,7 @@ def _gates(a, u, s, vt, s_ref, precision=0):
 def _fallback_consistent(info):
     import paper_2609_32505_gb300 as P
     for i in info:
-        bad = not (i["corr_max"] <= P.MIXED_CORR_MAX) or not (i["range_resid"] <= P.MIXED_RANGE_MAX)
+        bad = not (i["corr_max"] <= P.MIXED_CORR_MAX) or not (i["recon_est"] <= P.MIXED_RECON_MAX)
         assert i["prec_fallback"] == int(bad)
 
 
@@ -142,15 +142,29 @@ def test_mixed_keeps_large_well_conditioned_result():
     assert O.ortho_error(u) <= 1e-4 and O.ortho_error(vt.T) <= 1e-4
 
 
-def test_mixed_range_check_on_tall_input():
-    # m > n: the low-precision steps tilt the column space of W; the range residual
-    # flags it and the result still meets the gates
+def test_mixed_reconstruction_check_on_tall_input():
+    # m > n: the low-precision steps tilt the column space of W; the probe estimate of the
+    # reconstruction error sees it, and the result still meets the gates
     a, _, _ = W.constructed(8, 260, 100, W.kappa_spectrum(100, 10.0))
     a = a.astype(np.float32).astype(np.float64)
     u, s, vt, info = _svd(a, precision=1)
     _fallback_consistent(info)
-    assert info[0]["range_resid"] > 0
+    assert info[0]["recon_est"] > 0
     _gates(a, u, s, vt, O.svd(a)[1], 1)
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mixed_reconstruction_estimate_tracks_the_error(precision):
+    # the 8-probe estimate of ||A - U S V^T||_F / ||A||_F against the error of the returned
+    # factors, where the mixed result was kept (after a fallback the record still holds the
+    # mixed attempt's estimate, while the factors come from the FP32-accurate rerun)
+    a, _, _ = W.constructed(9, 1024, 1024, W.kappa_spectrum(1024, 10.0))
+    a = a.astype(np.float32).astype(np.float64)
+    u, s, vt, info = _svd(a, precision=precision)
+    _fallback_consistent(info)
+    if info[0]["prec_fallback"] == 0:
+        err = O.recon_error(a, u, s, vt)
+        assert 0.3 * err <= info[0]["recon_est"] <= 3.0 * err + 1e-7
 
 
 def test_mixed_learned_gate_on_small_lower_bound():
