@@ -198,6 +198,19 @@ int psvd_polar_bwd(const float *A, const float *W, const float *H, const float *
                    const float *dH, float *dA, int64_t batch, int64_t m, int64_t n,
                    double eps, void *ws, size_t ws_bytes, void *stream);
 
+/* psvd_eigh_bwd -- the EVD pseudo-gradient of Theorem 4.3 for H = V diag(S) V^T (as returned
+ *   by psvd_eigh): Hbar = V (diag(Sbar) + 1/2 K^T o (V^T Vbar - Vbar^T V)) V^T, with
+ *   Vbar = dVT^T the gradient of V.  kreg_mode selects K as for psvd_svd_bwd: 0 = Tikhonov
+ *   K_eps with eps^(1/2) (Algorithm 4's form), 1 = K_eps with eps^2 (Section 5.2's form),
+ *   2 = exact 1/(s_i - s_j) with ties (|s_i - s_j| <= 1e-6 s_max) masked (eps must then be 0,
+ *   and eps > 0 otherwise).  S: batch x n, VT: batch x n x n (rows = eigenvectors);
+ *   dS (batch x n) and dVT (batch x n x n) may be NULL (zero).  dH: batch x n x n out
+ *   (symmetric).  Three split-TF32 products of n^3 each. */
+size_t psvd_eigh_bwd_workspace_bytes(int64_t batch, int64_t n);
+int psvd_eigh_bwd(const float *S, const float *VT, const float *dS, const float *dVT, float *dH,
+                  int64_t batch, int64_t n, double eps, int kreg_mode, void *ws, size_t ws_bytes,
+                  void *stream);
+
 /* ---- learned schedule (the lower-bound predictor) ---------------------------
  * psvd_sketch_features -- 8 features per matrix of X0 = M / sqrt(||M||_1 ||M||_inf):
  *   logs of Hutchinson estimates of tr(G^k)/n, k = 1..4 (G = X0^T X0) with the caller's

@@ -30,7 +30,8 @@ What each function computes, with the passage it follows:
                            decomposition of the n x n factor R, then U = Q U_R, W = Q W_R,
                            H = H_R.
 * ``polar_bwd``            Algorithm 3 / Proposition 3.2 (regularized), Theorem 3.1 (eps=0).
-* ``evd_bwd``              Theorem 4.3 (EVD pseudo-gradient).
+* ``evd_bwd``              Theorem 4.3 (EVD pseudo-gradient), and its K_eps regularization
+                           (Section 5.2).
 * ``svd_bwd``              Algorithm 4 (complete pipeline), kreg modes 0/1/2.
 * ``svd_bwd_townsend``     Theorem G.1 (distinct spectra, thin, m >= n).
 * ``svd_bwd_degenerate``   Theorem H.1 (square, repeated singular values allowed).
@@ -414,13 +415,22 @@ def polar_bwd_thm31(m, w, h, wbar, hbar):
     return wbar @ hinv + 2.0 * np.asarray(m, dtype=np.float64) @ x
 
 
-def evd_bwd(v, sigma, vbar, sigmabar, tie_tol: float = 0.0):
+def evd_bwd(v, sigma, vbar, sigmabar, tie_tol: float = 0.0, eps: float = 0.0, kreg_mode: int = 2):
     """Theorem 4.3: K_ij = 1/(s_i - s_j) (0 on equal values), S = 1/2 K^T o (V^T Vbar - Vbar^T V),
-    Mbar_star = V (S + diag(sigmabar)) V^T."""
+    Mbar_star = V (S + diag(sigmabar)) V^T.
+
+    With kreg_mode 0 or 1, K is replaced by its Tikhonov regularization K_eps (Section 5.2,
+    the paragraph after Theorem 4.3): (s_i - s_j) / ((s_i - s_j)^2 + reg) with reg = eps^(1/2)
+    (the form Algorithm 4 prints, mode 0) or eps^2 (the form Section 5.2 prints, mode 1).
+    ``vbar`` or ``sigmabar`` may be None (zero)."""
+    v = np.asarray(v, dtype=np.float64)
     s = np.asarray(sigma, dtype=np.float64)
-    k = _k_mask(s, 0.0, 2, tie_tol)
+    n = s.shape[0]
+    vbar = np.zeros((n, n)) if vbar is None else np.asarray(vbar, dtype=np.float64)
+    sbar = np.zeros(n) if sigmabar is None else np.asarray(sigmabar, dtype=np.float64)
+    k = _k_mask(s, eps, kreg_mode, tie_tol)
     smat = 0.5 * k.T * (v.T @ vbar - vbar.T @ v)
-    return v @ (smat + np.diag(sigmabar)) @ v.T
+    return v @ (smat + np.diag(sbar)) @ v.T
 
 
 def svd_bwd(m, u, sigma, vt, ubar, sigmabar, vtbar, eps: float = 1e-8,

@@ -80,6 +80,8 @@ def lib():
                                         ctypes.c_int, vp, sz, vp]),
         "psvd_polar_bwd_workspace_bytes": (sz, [i64, i64, i64]),
         "psvd_polar_bwd": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, i64, i64, i64, ctypes.c_double, vp, sz, vp]),
+        "psvd_eigh_bwd_workspace_bytes": (sz, [i64, i64]),
+        "psvd_eigh_bwd": (ctypes.c_int, [vp, vp, vp, vp, vp, i64, i64, ctypes.c_double, ctypes.c_int, vp, sz, vp]),
         "psvd_profile_enable": (ctypes.c_int, [ctypes.c_int]),
         "psvd_sketch_workspace_bytes": (sz, [i64, i64, i64, i64]),
         "psvd_sketch_features": (ctypes.c_int, [vp, vp, i64, vp, i64, i64, i64, vp, sz, vp]),
@@ -239,6 +241,44 @@ def polar_bwd(a, w, h, dw=None, dh=None, eps: float = 1e-8):
     _check(L.psvd_polar_bwd(_ptr(A), _ptr(Wt), _ptr(H), _ptr(dW), _ptr(dH), _ptr(dA), bt, m, n, float(eps),
                             _ptr(ws), ws.numel(), _stream()), "psvd_polar_bwd")
     return dA[0] if sq else dA
+
+
+def eigh_bwd(s, vt, ds=None, dvt=None, eps: float = 1e-8, kreg_mode: int = 0):
+    """Theorem 4.3 backward of H = V diag(S) V^T (psvd_eigh_bwd): the symmetric dH from the
+    gradients of S and V^T (None = zero), with K_eps chosen by kreg_mode."""
+    S = s.contiguous().float()
+    sq = S.dim() == 1
+    S = S.reshape(-1, S.shape[-1])
+    bt, n = S.shape
+    VT = vt.contiguous().float().reshape(bt, n, n)
+    dS, dVT = _opt(ds, (bt, n)), _opt(dvt, (bt, n, n))
+    dH = torch.empty(bt, n, n, device=S.device, dtype=torch.float32)
+    L = lib()
+    ws = _workspace(L.psvd_eigh_bwd_workspace_bytes(bt, n), S.device)
+    _check(L.psvd_eigh_bwd(_ptr(S), _ptr(VT), _ptr(dS), _ptr(dVT), _ptr(dH), bt, n, float(eps), int(kreg_mode),
+                           _ptr(ws), ws.numel(), _stream()), "psvd_eigh_bwd")
+    return dH[0] if sq else dH
+
+
+class _EighFunction(torch.autograd.Function):
+    """Forward: psvd_eigh.  Backward: psvd_eigh_bwd (Theorem 4.3 with K_eps)."""
+
+    @staticmethod
+    def forward(ctx, h, eps, kreg_mode):
+        s, vt = eigh(h)
+        ctx.save_for_backward(s, vt)
+        ctx.eps, ctx.kreg = eps, kreg_mode
+        return s, vt
+
+    @staticmethod
+    def backward(ctx, gs, gvt):
+        s, vt = ctx.saved_tensors
+        return eigh_bwd(s, vt, gs, gvt, ctx.eps, ctx.kreg), None, None
+
+
+def eigh_ad(h: torch.Tensor, eps: float = 1e-8, kreg_mode: int = 0):
+    """Differentiable symmetric EVD: returns (S descending, V^T); gradients by Theorem 4.3."""
+    return _EighFunction.apply(h, eps, kreg_mode)
 
 
 class _SVDFunction(torch.autograd.Function):

@@ -303,9 +303,115 @@ int polar_backward(const float *A, const float *H, const float *dW, const float 
 }
 
 
+// ------------------------------------------------------------ EVD backward (Theorem 4.3)
+// Hbar = V (diag(Sbar) + 1/2 K^T o (P - P^T)) V^T with P = V^T Vbar, K replaced by its
+// Tikhonov regularization K_eps (Section 5.2) in modes 0 and 1.  The middle factor E is
+// symmetric (K^T and P - P^T are both skew), so V E and (V E) V^T are both TN products
+// with V row-major as an operand.
+struct EvdBwdWS {
+    int B = 0, n = 0;
+    long long ldn = 0;
+    float *VThi = nullptr, *VTlo = nullptr, *Vhi = nullptr, *Vlo = nullptr;
+    float *dVThi = nullptr, *dVTlo = nullptr, *P = nullptr;
+    float *Ehi = nullptr, *Elo = nullptr, *Zhi = nullptr, *Zlo = nullptr;
+    unsigned *err = nullptr;
+    template <class C>
+    void carve(C &cv, int B_, int n_) {
+        B = B_; n = n_; ldn = pad_ld(n);
+        const long long B64 = B, nn = (long long)n * ldn;
+        VThi = cv.template take<float>(B64 * nn); VTlo = cv.template take<float>(B64 * nn);
+        Vhi = cv.template take<float>(B64 * nn); Vlo = cv.template take<float>(B64 * nn);
+        dVThi = cv.template take<float>(B64 * nn); dVTlo = cv.template take<float>(B64 * nn);
+        P = cv.template take<float>(B64 * n * n);
+        Ehi = cv.template take<float>(B64 * nn); Elo = cv.template take<float>(B64 * nn);
+        Zhi = cv.template take<float>(B64 * nn); Zlo = cv.template take<float>(B64 * nn);
+        err = cv.template take<unsigned>(4);
+    }
+};
+
+// E_ij = delta_ij Sbar_i - 1/2 K_ij (P_ij - P_ji)   ((K^T)_ij = K_ji = -K_ij), split TF32.
+__global__ void evd_core_kernel(const float *P, const float *S, const float *dS, int n, float eps, int kreg_mode,
+                                float tie_tol, float *Ehi, float *Elo, long long ld) {
+    const int b = blockIdx.z;
+    const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
+    if (i >= n || j >= n) return;
+    const long long bo = (long long)b * n * n;
+    const float *s = S + (long long)b * n;
+    const float d = s[i] - s[j];
+    float kij;
+    if (kreg_mode == 0) kij = d / (d * d + sqrtf(eps));
+    else if (kreg_mode == 1) kij = d / (d * d + eps * eps);
+    else {
+        const float smax = fmaxf(fabsf(s[0]), fabsf(s[n - 1]));
+        kij = fabsf(d) <= tie_tol * smax ? 0.f : 1.f / d;
+    }
+    const float pij = P ? P[bo + (long long)i * n + j] : 0.f, pji = P ? P[bo + (long long)j * n + i] : 0.f;
+    float e = -0.5f * kij * (pij - pji);
+    if (i == j) e = dS ? dS[(long long)b * n + i] : 0.f;
+    float h, l;
+    split_tf32(e, h, l);
+    Ehi[(long long)b * n * ld + (long long)i * ld + j] = h;
+    Elo[(long long)b * n * ld + (long long)i * ld + j] = l;
+}
+
+int eigh_backward(const float *S, const float *VT, const float *dS, const float *dVT, float *dH, EvdBwdWS &w,
+                  double eps, int kreg, cudaStream_t st) {
+    const int B = w.B, n = w.n;
+    const long long ldn = w.ldn, nn = (long long)n * ldn;
+    PSVD_TRY(prepare_operand(VT, n, (long long)n * n, B, n, n, false, 1.f, nullptr, so(w.VThi, w.VTlo, ldn, nn), st));
+    PSVD_TRY(prepare_operand(VT, n, (long long)n * n, B, n, n, true, 1.f, nullptr, so(w.Vhi, w.Vlo, ldn, nn), st));
+    if (dVT) {
+        PSVD_TRY(prepare_operand(dVT, n, (long long)n * n, B, n, n, false, 1.f, nullptr, so(w.dVThi, w.dVTlo, ldn, nn),
+                                 st));
+        // P = V^T Vbar: P[i][k] = sum_j VT[i][j] dVT[k][j]
+        EpiStore e = epi_store_plain(w.P, n, (long long)n * n, n, n);
+        PSVD_TRY_RC(g3(w.VThi, w.VTlo, n, n, ldn, nn, w.dVThi, w.dVTlo, n, ldn, nn, B, e, w.err, st));
+    }
+    dim3 g16((n + 15) / 16, (n + 15) / 16, B), b16(16, 16);
+    evd_core_kernel<<<g16, b16, 0, st>>>(dVT ? w.P : nullptr, S, dS, n, kreg == 2 ? 0.f : (float)eps, kreg, 1e-6f,
+                                         w.Ehi, w.Elo, ldn);
+    count_launch(1);
+    PSVD_TRY(cudaGetLastError());
+    {   // Z = V E (E symmetric, so the B operand B[k][j] = E[j][k] is E itself)
+        EpiStore e;
+        memset(&e, 0, sizeof(e));
+        e.rows = n; e.cols = n; e.alpha = 1.f;
+        e.hi = w.Zhi; e.lo = w.Zlo; e.ldh = ldn; e.bsh = nn;
+        PSVD_TRY_RC(g3(w.Vhi, w.Vlo, n, n, ldn, nn, w.Ehi, w.Elo, n, ldn, nn, B, e, w.err, st));
+    }
+    {   // Hbar = Z V^T: B operand B[k][j] = V^T[j][k] = V[k][j], V row-major
+        EpiStore e = epi_store_plain(dH, n, (long long)n * n, n, n);
+        PSVD_TRY_RC(g3(w.Zhi, w.Zlo, n, n, ldn, nn, w.Vhi, w.Vlo, n, ldn, nn, B, e, w.err, st));
+    }
+    return cudaGetLastError() == cudaSuccess ? PSVD_OK : PSVD_ERR_CUDA;
+}
+
 }  // namespace psvd
 
 using namespace psvd;
+
+extern "C" size_t psvd_eigh_bwd_workspace_bytes(int64_t batch, int64_t n) {
+    if (batch <= 0 || n <= 0) return 0;
+    Sizer s;
+    EvdBwdWS w;
+    w.carve(s, (int)batch, (int)n);
+    return s.used + 256;
+}
+
+extern "C" int psvd_eigh_bwd(const float *S, const float *VT, const float *dS, const float *dVT, float *dH,
+                             int64_t batch, int64_t n, double eps, int kreg_mode, void *ws, size_t ws_bytes,
+                             void *stream) {
+    if (!S || !VT || !dH || batch <= 0 || n <= 0 || batch > 65535 || n > 16384 || kreg_mode < 0 || kreg_mode > 2 ||
+        !(eps >= 0.0) || (eps == 0.0 && kreg_mode != 2))
+        return PSVD_ERR_ARG;
+    if (int e = check_device()) return e;
+    if (ws_bytes < psvd_eigh_bwd_workspace_bytes(batch, n)) return PSVD_ERR_WORKSPACE;
+    Carver cv(ws, ws_bytes);
+    EvdBwdWS w;
+    w.carve(cv, (int)batch, (int)n);
+    if (cv.overflow) return PSVD_ERR_WORKSPACE;
+    return eigh_backward(S, VT, dS, dVT, dH, w, eps, kreg_mode, static_cast<cudaStream_t>(stream));
+}
 
 extern "C" size_t psvd_svd_bwd_workspace_bytes(int64_t batch, int64_t m, int64_t n) {
     if (batch <= 0 || m <= 0 || n <= 0) return 0;

@@ -5,6 +5,9 @@
   python -m paper_2609_32505_gb300.microbench eigh  --n 4096
   python -m paper_2609_32505_gb300.microbench svd   --n 4096 --prec 0|1
   python -m paper_2609_32505_gb300.microbench stages --n 4096
+  python -m paper_2609_32505_gb300.microbench budget --n 4096 --prec 0|1 [--learned]
+      (polar_fwd with the default step budget against one trimmed to the steps the input needs:
+       the difference is the time of the launches that found nothing left to do)
 
 Inputs are A = Q1 diag(s) Q2^T with s_i = kappa^((n-i)/(n-1)) (kappa = 10 by default),
 generated on the device.  `--reps 1 --warmup 1` keeps a profiler capture to a couple of
@@ -43,7 +46,7 @@ def _time(f, reps: int, warmup: int) -> float:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["gemm", "polar", "eigh", "svd", "stages"])
+    ap.add_argument("what", choices=["gemm", "polar", "eigh", "svd", "stages", "budget"])
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--m", type=int, default=0)
     ap.add_argument("--batch", type=int, default=1)
@@ -66,12 +69,27 @@ def main(argv=None):
         print(f"gemm_tn n={n} prec={a.prec}: {ms:.3f} ms, {2 * n ** 3 / ms / 1e9:.1f} TFLOP/s (operand split included)")
         return
     o = P.make_opts(precision=a.prec)
+    lb = None
     if a.learned:
         # an oracle-free stand-in for the learned bound: 0.9 sigma_min(X0), from the known
         # spectrum (sigma_min(A) = 1) and the normalization scale the iteration reports
         _, _, info = P.polar(A, o, want_h=False, return_info=True)
         lb = torch.tensor([0.9 / i["scale"] for i in info], device=dev, dtype=torch.float32)
         o = P.make_opts(precision=a.prec, schedule=P.SCHED_LEARNED, lower_bound=lb)
+    if a.what == "budget":
+        _, _, info = P.polar(A, o, want_h=False, return_info=True)
+        used = max(i["iters"] for i in info)
+        full = _time(lambda: P.polar(A, o, want_h=False), a.reps, a.warmup)
+        kw = dict(precision=a.prec, max_iter=max(1, used + 1 - (2 if not a.learned else 0)))
+        if a.learned:
+            kw.update(schedule=P.SCHED_LEARNED, lower_bound=lb, budget=used + 1)
+        ot = P.make_opts(**kw)
+        _, _, info_t = P.polar(A, ot, want_h=False, return_info=True)
+        assert all(i["status"] == 0 for i in info_t), info_t
+        trim = _time(lambda: P.polar(A, ot, want_h=False), a.reps, a.warmup)
+        print(f"budget n={n} prec={a.prec} learned={a.learned}: steps used {used}; default budget {full:.3f} ms, "
+              f"trimmed {trim:.3f} ms, empty launches {full - trim:.3f} ms", flush=True)
+        return
     if a.what in ("polar", "stages"):
         ms = _time(lambda: P.polar(A, o), a.reps, a.warmup)
         _, _, info = P.polar(A, o, return_info=True)

@@ -38,17 +38,22 @@ def test_polar_parity(m, n, kappa, precision):
         assert np.abs(w - w_ref).max() < 2e-5 * max(1.0, kappa / 1e3)
         assert np.abs(h - h_ref).max() < 2e-5 * s[0]
     else:
-        # BF16/TF32 steps rotate X inside low-sigma subspaces (invisible to the
-        # orthogonality residual, kept by later steps); H = (W^T A)_sym is still an
-        # FP32-accurate product, so A - W H = W skew(W^T A) is that rotation's footprint.
-        # Bound: the paper's all-TF32 variant reaches ||A - U S V^T||_F / ||A||_F <= 1.2e-3
-        # at every kappa of Table 1; here only the polynomial steps are low precision, so
-        # TF32 stays within 2e-3, and BF16 (unit roundoff 2^-9, four times TF32's 2^-11)
-        # within four times that.
+        # BF16/TF32 steps rotate X inside low-sigma subspaces and, for m > n, tilt it out of
+        # its column space (invisible to the orthogonality residual, kept by later steps); H is
+        # still an FP32-accurate product, so ||A - W H||_F / ||A||_F is that rounding's footprint.
+        # A rounding error made at step k in the direction of a right singular vector v_i is
+        # amplified by the growth still ahead of sigma_i (1 / sigma_i^(k)) and weighted by
+        # sigma_i(A) in A, so each step contributes O(u) relative to ||A||, independently of
+        # kappa; the steps' errors are independent, so they add like sqrt(K).  Bound:
+        # 4 u sqrt(K), u the unit roundoff of the step precision (TF32 2^-11, BF16 2^-8) and K
+        # the number of low-precision steps.  (Measured at 300 x 200, kappa = 1e3: 4.2e-3 TF32,
+        # 3.4e-2 BF16 -- the ratio of the two unit roundoffs; the paper's all-TF32 variant gives
+        # about 1e-3 at 4096^2, Table 1.)
         low = "steps_bf16" if precision == 2 else "steps_tf32"
         assert info[0][low] > 0 and info[0]["steps_3xtf32"] > 0
-        bound = 2e-3 if precision == 1 else 8e-3
-        assert np.linalg.norm(a32 - w @ h) / np.linalg.norm(a32) < bound
+        k_low = info[0]["steps_bf16"] + info[0]["steps_tf32"]
+        u = 2.0 ** -11 if precision == 1 else 2.0 ** -8
+        assert np.linalg.norm(a32 - w @ h) / np.linalg.norm(a32) < 4.0 * u * np.sqrt(k_low)
 
 
 def test_polar_batch_and_schedules():

@@ -173,3 +173,45 @@ def test_pins_catch_swapped_exponents(monkeypatch, which):
             test_polar_bwd_regularized_wbar_diagonal(1e-4)
         else:
             test_svd_bwd_kreg_two_by_two(0 if which == "k0" else 1, 1.01, 1.0, 1e-4)
+
+
+# ---------------------------------------------------------------- EVD backward (Theorem 4.3 with K_eps)
+def _evd_two_by_two(s1, s2, a_skew, sb1, sb2, eps, mode, th):
+    """Theorem 4.3 by hand for H = V diag(s1, s2) V^T (V a rotation), Vbar = V Omega with
+    Omega = [[0, a], [-a, 0]], Sbar = diag(sb1, sb2).
+
+    V^T Vbar = Omega and V^T Vbar - Vbar^T V = 2 Omega, so S = K^T o Omega:
+    S_12 = K_21 a = -K_12 a and S_21 = K_12 (-a) = -K_12 a, with K_12 = d / (d^2 + reg),
+    d = s1 - s2 (reg = eps^(1/2) in mode 0, eps^2 in mode 1; mode 2: 1/d).
+    Hbar = V [[sb1, -K_12 a], [-K_12 a, sb2]] V^T."""
+    d = s1 - s2
+    k12 = d / (d * d + math.sqrt(eps)) if mode == 0 else (d / (d * d + eps * eps) if mode == 1 else 1.0 / d)
+    core = np.array([[sb1, -k12 * a_skew], [-k12 * a_skew, sb2]])
+    v = _rotation(th)
+    return v @ core @ v.T, v
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("s1,s2,eps", [(1.01, 1.0, 1e-4), (3.0, 0.5, 1.0), (2.0, 1.999, 1e-8), (1.2, 1.0, 10.0)])
+def test_evd_bwd_kreg_two_by_two(mode, s1, s2, eps):
+    want, v = _evd_two_by_two(s1, s2, 0.53, 0.7, -1.3, eps, mode, 0.83)
+    vbar = v @ np.array([[0.0, 0.53], [-0.53, 0.0]])
+    got = O.evd_bwd(v, np.array([s1, s2]), vbar, np.array([0.7, -1.3]), eps=eps, kreg_mode=mode)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-14 * max(1.0, np.abs(want).max()))
+
+
+def test_evd_bwd_regularized_tends_to_thm43():
+    # K_eps -> K as eps -> 0 on a distinct spectrum (the limit stated after Theorem 4.3)
+    rng = W.rng_for(740)
+    n = 6
+    v = W.orthonormal(rng, n, n)
+    s = np.sort(rng.uniform(0.5, 3.0, n))[::-1]
+    vbar, sbar = rng.standard_normal((n, n)), rng.standard_normal(n)
+    exact = O.evd_bwd(v, s, vbar, sbar)
+    for mode in (0, 1):
+        gaps = []
+        for eps in (1e-2, 1e-4, 1e-8, 1e-12, 1e-16):
+            gaps.append(np.linalg.norm(O.evd_bwd(v, s, vbar, sbar, eps=eps, kreg_mode=mode) - exact))
+        ref = np.linalg.norm(exact)
+        assert all(b < a or b < 1e-14 * ref for a, b in zip(gaps, gaps[1:]))
+        assert gaps[-1] < 1e-5 * ref
