@@ -63,6 +63,11 @@ extern "C" {
 #define PSVD_SCHED_LEARNED  1 /* greedy optimal cubics from [l_b, 1], l_b a predicted lower
                                  bound of sigma_min(X0) per matrix (opts.lower_bound)       */
 #define PSVD_SCHED_NS       2 /* classical Newton-Schulz, p(x) = 1.5 x - 0.5 x^3           */
+#define PSVD_SCHED_PE       3 /* comparison schedule of the polar-iteration ablation (Appendix B),
+                                 Polar-Express style: the greedy optimal cubics of schedule 1
+                                 from [l_b, 1] (opts.lower_bound), each applied to x / 1.01 while
+                                 the tracked interval is wider than 1e-2, then undamped.  No
+                                 conservative rerun.                                          */
 
 typedef struct psvd_opts {
     int    precision;     /* PSVD_PREC_*                                        default 0    */
@@ -75,6 +80,10 @@ typedef struct psvd_opts {
     const float *lower_bound; /* DEVICE [batch]: schedule 1's lower bounds (NULL otherwise) */
     int    budget;        /* schedule 1: steps allowed before the conservative rerun
                              (0 = automatic: predicted steps + 5)                           */
+    double *res_history;  /* DEVICE [(max_iter + pre_iters + 1) x batch] or NULL: entry
+                             k * batch + b receives ||X_k^T X_k - I||_F / sqrt(n) at step k
+                             of matrix b (0 once it has finished; for schedule 1 the steps of
+                             the last pass, i.e. of the conservative rerun where there was one) */
 } psvd_opts;
 
 /* Fills *o with the defaults above (host pointer). */

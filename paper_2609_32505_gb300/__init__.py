@@ -19,7 +19,7 @@ _LIB_PATH = os.path.join(_PKG, "libpsvd.so")
 _lib = None
 
 PREC_FP32, PREC_MIXED, PREC_MIXED_BF16 = 0, 1, 2
-SCHED_CANS, SCHED_LEARNED, SCHED_NS = 0, 1, 2
+SCHED_CANS, SCHED_LEARNED, SCHED_NS, SCHED_PE = 0, 1, 2, 3
 GEMM_BF16, GEMM_TF32, GEMM_TF32X3 = 0, 1, 2
 
 STATUS = {0: "ok", 1: "not_converged", -1: "arg", -2: "workspace", -3: "nonfinite", -4: "cuda",
@@ -35,7 +35,8 @@ class PsvdError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("schedule", ctypes.c_int), ("delta", ctypes.c_double),
                 ("pre_iters", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
-                ("eps_qr", ctypes.c_double), ("lower_bound", ctypes.c_void_p), ("budget", ctypes.c_int)]
+                ("eps_qr", ctypes.c_double), ("lower_bound", ctypes.c_void_p), ("budget", ctypes.c_int),
+                ("res_history", ctypes.c_void_p)]
 
 
 INFO_FIELDS = ["status", "iters", "qr_fallback", "sched_fallback", "prec_fallback", "steps_bf16", "steps_tf32",
@@ -140,12 +141,14 @@ def gemm_tn(a: torch.Tensor, b: torch.Tensor, precision: int = GEMM_TF32X3) -> t
 
 
 def make_opts(precision: int = PREC_FP32, schedule: int = SCHED_CANS, delta: float = 0.99, pre_iters: int = 2,
-              max_iter: int = 50, tol: float = 1e-5, eps_qr: float = 1e-5, lower_bound=None, budget: int = 0):
+              max_iter: int = 50, tol: float = 1e-5, eps_qr: float = 1e-5, lower_bound=None, budget: int = 0,
+              res_history=None):
     o = Opts()
     lib().psvd_default_opts(ctypes.byref(o))
     o.precision, o.schedule, o.delta, o.pre_iters = precision, schedule, delta, pre_iters
     o.max_iter, o.tol, o.eps_qr, o.budget = max_iter, tol, eps_qr, budget
     o.lower_bound = None if lower_bound is None else lower_bound.data_ptr()
+    o.res_history = None if res_history is None else res_history.data_ptr()
     return o
 
 

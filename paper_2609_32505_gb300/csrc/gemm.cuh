@@ -72,6 +72,7 @@ struct GemmShape {
     const int *skip;        // [batch] nonzero = matrix finished, its tiles are skipped (or nullptr)
     const int *gate;        // nullptr, or a device counter: 0 = nothing left to do, the whole launch
                             // returns at once (written by an earlier kernel on the same stream)
+    unsigned *ticket;       // nullptr, or a zeroed counter: the last CTA to finish runs epi.tail()
     unsigned *err;          // device error word
 };
 
@@ -140,6 +141,11 @@ template <class E> struct EpiHasTrans<E, std::void_t<decltype(E::kTrans)>> : std
 // after the previous element's store (one read in flight per thread).
 template <class E, class = void> struct EpiHasPre : std::false_type {};
 template <class E> struct EpiHasPre<E, std::void_t<decltype(E::kPre)>> : std::integral_constant<bool, E::kPre> {};
+// Epilogues with a tail() run it once per launch, in the last CTA to finish (shp.ticket set),
+// after every CTA's epilogue writes and atomics are visible: a per-launch reduction step
+// (the polar iteration's per-matrix decision) without a launch of its own.
+template <class E, class = void> struct EpiHasTail : std::false_type {};
+template <class E> struct EpiHasTail<E, std::void_t<decltype(E::kTail)>> : std::integral_constant<bool, E::kTail> {};
 
 // Consumer side of the operand ring, as seen by the MMA issuer: shared-memory address of
 // unit 0, unit size, unit count, barriers, and the position of the next unit with the
@@ -413,6 +419,18 @@ gemm_tn_kernel(const __grid_constant__ GemmMaps maps, const GemmShape shp, Epi e
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, kTmemCols);
+    }
+    if constexpr (EpiHasTail<Epi>::value) {
+        if (shp.ticket) {
+            __shared__ int s_last;
+            if (threadIdx.x == 0) {
+                __threadfence();                                  // this CTA's writes before its ticket
+                s_last = atomicAdd(shp.ticket, 1u) == gridDim.x - 1;
+                if (s_last) __threadfence();                      // every other CTA's, before the tail
+            }
+            __syncthreads();
+            if (s_last) epi.tail();
+        }
     }
 }
 

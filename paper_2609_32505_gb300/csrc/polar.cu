@@ -104,12 +104,36 @@ struct CoefTable {
 // coef[(k * B + b) * 2 + {0,1}] for k < K.  Learned: greedy optimal cubics from
 // [l_b, 1] per matrix (FP64), and the step budget before the conservative rerun; with
 // gate_x3, a matrix whose bound is below PSVD_MIXED_LB_MIN starts on the split-TF32 rung.
+// Damped (the Polar-Express-style comparison schedule): the same greedy cubics from [l_b, 1]
+// applied to x / kPeDamp while the tracked interval is wider than kPeWidth, then undamped
+// from the interval reached; no budget (the comparison schedule has no fallback).
+constexpr double kPeDamp = 1.01, kPeWidth = 1e-2;
 __global__ void schedule_fill_kernel(int B, int K, CoefTable tab, const float *lower, int learned, double tol,
                                      int budget_opt, const int *active, float *coef, int *budget, int gate_x3,
-                                     int *prec) {
+                                     int *prec, int damped = 0) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     if (active && !active[b]) return;
+    if (damped) {
+        double l = (double)lower[b];
+        if (!(l > 1e-12)) l = 1e-12;
+        if (l > 0.999) l = 0.999;
+        double lo = l, hi = 1.0;
+        bool damping = true;
+        for (int k = 0; k < K; ++k) {
+            if (damping && fmax(1.0 - lo, hi - 1.0) <= kPeWidth) damping = false;
+            double nlo, nhi;
+            Cubic c;
+            if (damping) c = damped_cubic(lo, hi, kPeDamp, &nlo, &nhi);
+            else { c = cans_cubic(lo, hi); nlo = 1.0 - c.e; nhi = 1.0 + c.e; }
+            coef[((long long)k * B + b) * 2 + 0] = (float)c.c1;
+            coef[((long long)k * B + b) * 2 + 1] = (float)c.c3;
+            lo = nlo;
+            hi = nhi;
+        }
+        budget[b] = K;
+        return;
+    }
     if (!learned) {
         for (int k = 0; k < K; ++k) {
             const int i = k < tab.len ? k : tab.len - 1;
@@ -141,6 +165,43 @@ PSVD_DEV void store_prec(int p, long long o, float x, __nv_bfloat16 *p16, float 
     else { float h, l; split_tf32(x, h, l); phi[o] = h; plo[o] = l; }
 }
 
+// Per-matrix decision after the Gram of step k.
+// mixed: 0 every step split-TF32; 1 TF32 until the residual drops below kTauTF32; 2 BF16
+// above kTauBF16 first.  The precision never decreases from one step to the next.
+struct DecideArgs {
+    int k, B, n, mixed, learned, kcap;
+    double tol;
+    int *done, *fin, *status, *prec, *steps, *fallback, *notdone;
+    const double *res;
+    const int *budget;
+    float *fres;
+};
+
+PSVD_DEV void decide_matrix(const DecideArgs &d, int b) {
+    if (d.done[b]) return;
+    const int k = d.k, B = d.B;
+    const double r = sqrt(d.res[(long long)k * B + b] / (double)d.n);
+    const int pk = d.prec[(long long)k * B + b];
+    if (!(r <= 1e30)) {                              // NaN / overflow in the iteration
+        d.done[b] = 1; d.fin[b] = k; d.status[b] = PSVD_NOT_CONVERGED; d.fres[b] = (float)r;
+        return;
+    }
+    if (r <= d.tol) { d.done[b] = 1; d.fin[b] = k; d.status[b] = PSVD_OK; d.fres[b] = (float)r; return; }
+    if (k >= d.kcap) { d.done[b] = 1; d.fin[b] = k; d.status[b] = PSVD_NOT_CONVERGED; d.fres[b] = (float)r; return; }
+    if (d.learned && k >= d.budget[b]) {
+        d.done[b] = 1; d.fin[b] = k; d.status[b] = PSVD_NOT_CONVERGED; d.fres[b] = (float)r; d.fallback[b] = 1;
+        return;
+    }
+    int pn = PREC_TF32X3;
+    if (d.mixed) {
+        const int want = (d.mixed == 2 && r > kTauBF16) ? PREC_BF16 : (r > kTauTF32 ? PREC_TF32 : PREC_TF32X3);
+        pn = want > pk ? want : pk;
+    }
+    d.prec[(long long)(k + 1) * B + b] = pn;
+    d.steps[pk * B + b] += 1;
+    atomicAdd(&d.notdone[k], 1);
+}
+
 // Gram tile G = X^T X (tiles reaching the upper triangle): every entry with col >= row
 // adds to ||G - I||_F^2 (off-diagonal entries twice) and stores P = c1 I + c3 G and its
 // mirror in the precision of this step's apply; entries below the diagonal are left to
@@ -148,6 +209,7 @@ PSVD_DEV void store_prec(int p, long long o, float x, __nv_bfloat16 *p16, float 
 // (coalesced) element pass, the mirrors through trans() on the thread's own row.
 struct EpiGram {
     int n, B;
+    DecideArgs dec;      // this step's per-matrix decision, run by the launch's last CTA
     const float *coef;   // coef + k*B*2
     const int *prec;     // prec + k*B
     double *res;         // res + k*B
@@ -155,8 +217,11 @@ struct EpiGram {
     float *Phi, *Plo;
     long long ldp;
     struct Acc { double r; int p; float c1, c3; };
-    static constexpr bool kElem = true, kTrans = true;
+    static constexpr bool kElem = true, kTrans = true, kTail = true;
     PSVD_DEV bool staged() const { return true; }
+    PSVD_DEV void tail() const {
+        for (int b = threadIdx.x; b < dec.B; b += blockDim.x) decide_matrix(dec, b);
+    }
     PSVD_DEV void begin(Acc &a) const { a.r = 0.0; a.p = -1; }
     PSVD_DEV void load(Acc &a, int b) const {
         if (a.p < 0) { a.p = prec[b]; a.c1 = coef[2 * b]; a.c3 = coef[2 * b + 1]; }
@@ -228,36 +293,6 @@ struct EpiApply {
     PSVD_DEV void finish(Acc &, int, int, int) const {}
 };
 
-// Per-matrix decision after the Gram of step k.
-// mixed: 0 every step split-TF32; 1 TF32 until the residual drops below kTauTF32; 2 BF16
-// above kTauBF16 first.  The precision never decreases from one step to the next.
-__global__ void decide_kernel(int k, int B, int n, double tol, int mixed, int learned, int kcap, int *done,
-                              int *fin, int *status, int *prec, int *steps, const double *res, float *fres,
-                              const int *budget, int *fallback, int *notdone) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= B || done[b]) return;
-    const double r = sqrt(res[(long long)k * B + b] / (double)n);
-    const int pk = prec[(long long)k * B + b];
-    if (!(r <= 1e30)) {                              // NaN / overflow in the iteration
-        done[b] = 1; fin[b] = k; status[b] = PSVD_NOT_CONVERGED; fres[b] = (float)r;
-        return;
-    }
-    if (r <= tol) { done[b] = 1; fin[b] = k; status[b] = PSVD_OK; fres[b] = (float)r; return; }
-    if (k >= kcap) { done[b] = 1; fin[b] = k; status[b] = PSVD_NOT_CONVERGED; fres[b] = (float)r; return; }
-    if (learned && k >= budget[b]) {
-        done[b] = 1; fin[b] = k; status[b] = PSVD_NOT_CONVERGED; fres[b] = (float)r; fallback[b] = 1;
-        return;
-    }
-    int pn = PREC_TF32X3;
-    if (mixed) {
-        const int want = (mixed == 2 && r > kTauBF16) ? PREC_BF16 : (r > kTauTF32 ? PREC_TF32 : PREC_TF32X3);
-        pn = want > pk ? want : pk;
-    }
-    prec[(long long)(k + 1) * B + b] = pn;
-    steps[pk * B + b] += 1;
-    atomicAdd(&notdone[k], 1);
-}
-
 // W (user layout) from X_fin; leaves W split row-major in Xhi[0]/Xlo[0] and
 // transposed in XThi[0]/XTlo[0] for the products that follow (H, U).
 __global__ void polar_finalize_kernel(int m, int n, int B, const int *fin, const int *prec, const int *status,
@@ -311,6 +346,14 @@ __global__ void symmetrize_kernel(const float *Hraw, int n, float *Hsym, float *
     if (Hout) Hout[o] = (float)v;
 }
 
+// hist[k * B + b] = ||G_k - I||_F / sqrt(n) at the Gram of step k (0 where the matrix had
+// already finished, or the step was never reached).
+__global__ void res_history_kernel(const double *res, int K, int B, int n, double *hist) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= K * B) return;
+    hist[t] = sqrt(res[t] / (double)n);
+}
+
 __global__ void polar_info_kernel(int B, const int *status, const int *fin, const int *steps, const int *fallback,
                                   const float *fres, const float *scale, psvd_info *info) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -332,10 +375,11 @@ __global__ void polar_info_kernel(int B, const int *status, const int *fin, cons
 }
 
 // ------------------------------------------------------------ host driver
-// Step k: Gram (with the polynomial and residual epilogue), decision, apply.  The Gram
-// launch is gated on `gram_gate` (the count of matrices still iterating; nullptr = always
-// run) and the apply launch on this step's own count, so once every matrix has finished
-// the remaining launches of the budget return at once.
+// Step k: Gram (with the polynomial and residual epilogue, and the per-matrix decision run
+// by its last CTA), then apply.  The Gram launch is gated on `gram_gate` (the count of
+// matrices still iterating; nullptr = always run) and the apply launch on this step's own
+// count, so once every matrix has finished the remaining launches of the budget return at
+// once.
 static int launch_step(PolarWS &w, int k, bool apply, double tol, bool learned, float *fres, const int *gram_gate,
                        cudaStream_t st) {
     const int B = w.B, m = w.m, n = w.n;
@@ -351,9 +395,12 @@ static int launch_step(PolarWS &w, int k, bool apply, double tol, bool learned, 
         s.prec = w.prec + (long long)k * B;
         s.skip = w.done;
         s.gate = gram_gate;
+        s.ticket = w.ticket + k;
         s.err = w.err;
         EpiGram e;
         e.n = n; e.B = B;
+        e.dec = DecideArgs{k, B, n, w.bf16 ? 2 : (w.mixed ? 1 : 0), learned ? 1 : 0, w.kcap, tol, w.done, w.fin,
+                           w.status, w.prec, w.steps, w.fallback, w.notdone, w.res, w.budget, fres};
         e.coef = w.coef + (long long)k * B * 2;
         e.prec = w.prec + (long long)k * B;
         e.res = w.res + (long long)k * B;
@@ -362,12 +409,6 @@ static int launch_step(PolarWS &w, int k, bool apply, double tol, bool learned, 
                                      B, e, st);
         if (er != cudaSuccess) return PSVD_ERR_CUDA;
     }
-    const int ladder = w.bf16 ? 2 : (w.mixed ? 1 : 0);
-    decide_kernel<<<(B + 127) / 128, 128, 0, st>>>(k, B, n, tol, ladder, learned ? 1 : 0, w.kcap, w.done,
-                                                    w.fin, w.status, w.prec, w.steps, w.res, fres, w.budget,
-                                                    w.fallback, w.notdone);
-    count_launch(1);
-    if (cudaGetLastError() != cudaSuccess) return PSVD_ERR_CUDA;
     if (!apply) return PSVD_OK;
     // Apply: A = X (m x n, K = n), B = P (n x n, symmetric)
     {
@@ -437,7 +478,7 @@ static int prepare_x0(const float *A, PolarWS &w, cudaStream_t st, const int *sk
 }
 
 int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &w, const psvd_opts &o,
-                  psvd_info *info, cudaStream_t st) {
+                  psvd_info *info, cudaStream_t st, bool rerun_learned) {
     const int B = w.B, m = w.m, n = w.n;
     const bool learned = o.schedule == PSVD_SCHED_LEARNED;
     if (cudaMemsetAsync(w.rowsum, 0, sizeof(float) * (size_t)B * m, st) ||
@@ -445,6 +486,7 @@ int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &
         cudaMemsetAsync(w.nonfinite, 0, sizeof(int) * (size_t)B, st) ||
         cudaMemsetAsync(w.res, 0, sizeof(double) * (size_t)(w.kcap + 2) * B, st) ||
         cudaMemsetAsync(w.notdone, 0, sizeof(int) * (size_t)(w.kcap + 2), st) ||
+        cudaMemsetAsync(w.ticket, 0, sizeof(unsigned) * (size_t)(w.kcap + 2), st) ||
         cudaMemsetAsync(w.fres, 0, sizeof(float) * (size_t)B, st) ||
         cudaMemsetAsync(w.misc, 0, sizeof(int) * 8, st) ||
         cudaMemsetAsync(w.err, 0, sizeof(unsigned) * 4, st))
@@ -466,7 +508,7 @@ int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &
     const int gate_x3 = learned && w.mixed && !w.bf16 ? 1 : 0;
     schedule_fill_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, w.kcap + 1, tab, o.lower_bound, learned ? 1 : 0,
                                                           o.tol, o.budget, nullptr, w.coef, w.budget, gate_x3,
-                                                          w.prec);
+                                                          w.prec, o.schedule == PSVD_SCHED_PE ? 1 : 0);
     count_launch(1);
     if (int rc = prepare_x0(A, w, st, nullptr)) return rc;   // zero matrices get X0 = 0
     if (want_h) {
@@ -481,7 +523,7 @@ int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &
     int kmax = w.kcap;
     if (learned) kmax = std::min(w.kcap, o.budget > 0 ? o.budget : greedy_steps_to(1e-12, 0.5 * o.tol, w.kcap + 1) + 5);
     if (int rc = run_iteration(w, kmax, o.tol, learned, w.fres, nullptr, st)) return rc;
-    if (learned) {
+    if (learned && rerun_learned) {
         // Matrices whose learned schedule missed tol within budget are rerun from X0 with the
         // conservative schedule.  Nothing is read back: the rerun's steps are launched for the
         // whole budget, gated on the number of rerun matrices (misc[0]) and then on the
@@ -496,7 +538,8 @@ int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &
                                                               w.fallback, w.coef, w.budget, 0, w.prec);
         count_launch(1);
         if (cudaMemsetAsync(w.res, 0, sizeof(double) * (size_t)(w.kcap + 2) * B, st) ||
-            cudaMemsetAsync(w.notdone, 0, sizeof(int) * (size_t)(w.kcap + 2), st))
+            cudaMemsetAsync(w.notdone, 0, sizeof(int) * (size_t)(w.kcap + 2), st) ||
+            cudaMemsetAsync(w.ticket, 0, sizeof(unsigned) * (size_t)(w.kcap + 2), st))
             return PSVD_ERR_CUDA;
         if (int rc = prepare_x0(A, w, st, w.done)) return rc;
         if (int rc = run_iteration(w, w.kcap, o.tol, false, w.fres, w.misc, st)) return rc;
@@ -528,6 +571,11 @@ int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &
                                                            info);
         count_launch(1);
     }
+    if (o.res_history) {
+        const int K = w.kcap + 1;
+        res_history_kernel<<<(K * B + 127) / 128, 128, 0, st>>>(w.res, K, B, n, o.res_history);
+        count_launch(1);
+    }
     return cudaGetLastError() == cudaSuccess ? PSVD_OK : PSVD_ERR_CUDA;
 }
 
@@ -538,9 +586,10 @@ using namespace psvd;
 
 static bool opts_ok(const psvd_opts &o) {
     return (o.precision == PSVD_PREC_FP32 || o.precision == PSVD_PREC_MIXED || o.precision == PSVD_PREC_MIXED_BF16) &&
-           (o.schedule >= PSVD_SCHED_CANS && o.schedule <= PSVD_SCHED_NS) && o.delta > 0 && o.delta < 1 &&
+           (o.schedule >= PSVD_SCHED_CANS && o.schedule <= PSVD_SCHED_PE) && o.delta > 0 && o.delta < 1 &&
            o.pre_iters >= 0 && o.pre_iters <= 8 && o.max_iter >= 1 && o.max_iter <= 64 && o.tol > 0 &&
-           o.eps_qr > 0 && (o.schedule != PSVD_SCHED_LEARNED || o.lower_bound != nullptr);
+           o.eps_qr > 0 &&
+           ((o.schedule != PSVD_SCHED_LEARNED && o.schedule != PSVD_SCHED_PE) || o.lower_bound != nullptr);
 }
 
 static psvd_opts resolve_opts(const psvd_opts *p) {

@@ -34,6 +34,7 @@ struct PolarWS {
     double *res = nullptr;
     float *coef = nullptr, *fres = nullptr;
     int *misc = nullptr;
+    unsigned *ticket = nullptr;   // [kcap + 2] per-step CTA tickets of the Gram launches
     unsigned *err = nullptr;
 
     template <class C>
@@ -76,6 +77,7 @@ struct PolarWS {
         coef = cv.template take<float>((long long)(kcap + 1) * B64 * 2);
         fres = cv.template take<float>(B64);
         misc = cv.template take<int>(8);
+        ticket = cv.template take<unsigned>(kcap + 2);
         err = cv.template take<unsigned>(4);
     }
 };
@@ -87,8 +89,10 @@ inline int polar_kcap(const psvd_opts &o) { return o.max_iter + (o.schedule == P
 // split in Xhi[0]/Xlo[0].  If `want_h`, also computes Hsym = (W^T M)_sym (FP64
 // averaging) and copies it to H_out (may be null).  Never synchronizes: the step budget is
 // launched whole and finished matrices are skipped on the device.  Fills info (device,
-// may be null).
+// may be null).  With the learned schedule, matrices that miss tol within their budget
+// (ws.fallback) are rerun from X0 with the conservative schedule when `rerun_learned`;
+// otherwise they are left to the caller (svd_fwd recomputes them on its plain path).
 int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &ws, const psvd_opts &o,
-                  psvd_info *info, cudaStream_t st);
+                  psvd_info *info, cudaStream_t st, bool rerun_learned = true);
 
 }  // namespace psvd

@@ -69,6 +69,21 @@ inline std::vector<Cubic> cans_schedule(double delta, int pre, int total, double
     return out;
 }
 
+// Damped greedy cubic (the Polar-Express-style comparison schedule of the polar-iteration
+// ablation, Appendix B): the optimal cubic p for [a, b] applied to x / damp, i.e.
+// coefficients (c1 / damp, c3 / damp^3); the image of [a, b] under x -> p(x / damp) is
+// returned in [*lo, *hi] (p rises up to its interior maximum e and falls after it).
+__host__ __device__ inline Cubic damped_cubic(double a, double b, double damp, double *lo, double *hi) {
+    const Cubic c = cans_cubic(a, b);
+    auto p = [&](double y) { return c.c1 * y + c.c3 * y * y * y; };
+    const double ya = a / damp, yb = b / damp, e = sqrt(-c.c1 / (3.0 * c.c3));
+    double mn = fmin(p(ya), p(yb)), mx = fmax(p(ya), p(yb));
+    if (e > ya && e < yb) mx = fmax(mx, p(e));
+    *lo = mn;
+    *hi = mx;
+    return Cubic{c.c1 / damp, c.c3 / (damp * damp * damp), c.e};
+}
+
 // Steps of a greedy schedule from [a, 1] until the interval half-width is <= w.
 __host__ __device__ inline int greedy_steps_to(double a, double w, int cap) {
     double lo = a, hi = 1.0;

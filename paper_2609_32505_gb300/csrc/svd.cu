@@ -39,8 +39,14 @@ struct EpiColNorm {
     PSVD_DEV void finish(Acc &, int, int, int) const {}
 };
 
-__global__ void qr_flag_kernel(const float *colss, int n, double eps_qr, int *flag, int *any) {
+// skip: matrices the caller recomputes anyway (a learned schedule that fell back), whose
+// not-converged U must not start the QR fallback
+__global__ void qr_flag_kernel(const float *colss, int n, double eps_qr, const int *skip, int *flag, int *any) {
     const int b = blockIdx.x;
+    if (skip && skip[b]) {
+        if (threadIdx.x == 0) flag[b] = 0;
+        return;
+    }
     int bad = 0;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         const double nr = sqrt((double)colss[(long long)b * n + j]);
@@ -273,26 +279,35 @@ __global__ void __launch_bounds__(256) probe_resid_kernel(const float *A, const 
     }
 }
 
-// Matrices whose correction rotation or estimated reconstruction error is too large to
-// trust are flagged for the FP32-accurate rerun; records both in info.
-__global__ void mixed_flag_kernel(const unsigned *xmax, const double *sums, int B, float corr_limit,
-                                  float recon_limit, int *mflag, int *count, psvd_info *info) {
+// Matrices to recompute on the plain FP32-accurate path, with the reason as bits: 1 = the
+// mixed result's correction rotation or estimated reconstruction error is too large to
+// trust (mixed precision: xmax and sums given; both recorded in info), 2 = the learned
+// schedule missed tol within its budget (sched_fb given).
+__global__ void rerun_flag_kernel(const unsigned *xmax, const double *sums, const int *sched_fb, int B,
+                                  float corr_limit, float recon_limit, int *mflag, int *count, psvd_info *info) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
-    const float x = __uint_as_float(xmax[b]);
-    const float est = sums[2 * b] > 0.0 ? (float)sqrt(sums[2 * b + 1] / (kProbes * sums[2 * b])) : 0.f;
-    const int f = !(x <= corr_limit) || !(est <= recon_limit);
+    int f = 0;
+    if (xmax) {
+        const float x = __uint_as_float(xmax[b]);
+        const float est = sums[2 * b] > 0.0 ? (float)sqrt(sums[2 * b + 1] / (kProbes * sums[2 * b])) : 0.f;
+        if (!(x <= corr_limit) || !(est <= recon_limit)) f |= 1;
+        if (info) { info[b].corr_max = x; info[b].recon_est = est; }
+    }
+    if (sched_fb && sched_fb[b]) f |= 2;
     mflag[b] = f;
     if (f) atomicAdd(count, 1);
-    if (info) { info[b].corr_max = x; info[b].recon_est = est; }
 }
 
 // Results of the FP32-accurate rerun replace the flagged matrices' records.
-__global__ void info_scatter_kernel(psvd_info *info, const psvd_info *infoc, const int *idx, int F) {
+__global__ void info_scatter_kernel(psvd_info *info, const psvd_info *infoc, const int *idx, const int *whys,
+                                    int F) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= F) return;
     psvd_info r = infoc[j];
-    r.prec_fallback = 1;
+    const int why = whys[j];
+    r.prec_fallback = why & 1;
+    r.sched_fallback = (why >> 1) & 1;
     r.corr_max = info[idx[j]].corr_max;
     r.recon_est = info[idx[j]].recon_est;
     info[idx[j]] = r;
@@ -387,11 +402,12 @@ struct SvdWS {
     int *mflag = nullptr;
     double *rsums = nullptr;     // [B][2] reconstruction-check sums
     float *Yp = nullptr;         // [B][kProbes][n] sigma (V^T z) for the check
-    bool mixed = false;
+    bool mixed = false, learned = false;
 
     template <class C>
     void carve(C &cv, int B, int m, int n, const psvd_opts &o) {
         mixed = o.precision != PSVD_PREC_FP32;
+        learned = o.schedule == PSVD_SCHED_LEARNED;
         pw.carve(cv, B, m, n, polar_kcap(o), o.precision);
         ew.carve(cv, B, n, eigh_groups(B, n));
         const long long B64 = B, ld = pad_ld(n), nn = (long long)n * ld;
@@ -404,6 +420,7 @@ struct SvdWS {
         qbeta = cv.template take<float>(B64 * n);
         qbuf = cv.template take<float>(B64 * n * m);
         qbar = cv.template take<unsigned>(4);
+        mflag = cv.template take<int>(B64);
         if (mixed) {
             Vhi = cv.template take<float>(B64 * nn);
             Vlo = cv.template take<float>(B64 * nn);
@@ -420,7 +437,6 @@ struct SvdWS {
             Ft = cv.template take<float>(B64 * nn);
             VEt = cv.template take<float>(B64 * nn * 2);
             xmax = cv.template take<unsigned>(B64);
-            mflag = cv.template take<int>(B64);
             rsums = cv.template take<double>(B64 * 2);
             Yp = cv.template take<float>(B64 * kProbes * n);
         }
@@ -454,7 +470,8 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
     const int B = p.B, m = p.m, n = p.n;
     const long long ld = pad_ld(n), nn = (long long)n * ld;
     if (cudaMemsetAsync(w.any, 0, sizeof(int) * 4, st)) return PSVD_ERR_CUDA;
-    if (int rc = polar_forward(A, nullptr, nullptr, true, p, o, info, st)) return rc;
+    // a learned schedule's misses are recomputed with the rest of the rerun (below), not here
+    if (int rc = polar_forward(A, nullptr, nullptr, true, p, o, info, st, false)) return rc;
     if (int rc = eigh_forward(p.Hsym, Sout, nullptr, w.ew, st)) return rc;
     if (cudaMemcpyAsync(w.S, Sout, sizeof(float) * (size_t)B * n, cudaMemcpyDeviceToDevice, st)) return PSVD_ERR_CUDA;
     const float *vthi = w.ew.VThi, *vtlo = w.ew.VTlo;
@@ -515,7 +532,7 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
         hilo_store_kernel<<<g16, b16, 0, st>>>(vthi, vtlo, n, ld, VT);
         count_launch(1);
     }
-    qr_flag_kernel<<<B, 256, 0, st>>>(w.colss, n, o.eps_qr, w.flag, w.any);
+    qr_flag_kernel<<<B, 256, 0, st>>>(w.colss, n, o.eps_qr, w.learned ? p.fallback : nullptr, w.flag, w.any);
     count_launch(1);
     // QR fallback (Appendix A.2), decided on the device: the kernels run for the flagged
     // matrices only and return at once when none is flagged, so nothing is read back.
@@ -545,9 +562,13 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
         PSVD_TRY(cudaMemsetAsync(w.rsums, 0, sizeof(double) * 2 * (size_t)B, st));
         probe_vt_kernel<<<dim3((n + 7) / 8, B), 256, 0, st>>>(VT, Sout, n, w.Yp);
         probe_resid_kernel<<<dim3((m + 7) / 8, B), 256, 0, st>>>(A, U, w.Yp, m, n, w.rsums);
-        mixed_flag_kernel<<<(B + 127) / 128, 128, 0, st>>>(w.xmax, w.rsums, B, (float)PSVD_MIXED_CORR_MAX,
-                                                           (float)PSVD_MIXED_RECON_MAX, w.mflag, w.any + 1, info);
-        count_launch(3);
+        count_launch(2);
+    }
+    if (w.mixed || w.learned) {
+        rerun_flag_kernel<<<(B + 127) / 128, 128, 0, st>>>(
+            w.mixed ? w.xmax : nullptr, w.rsums, w.learned ? p.fallback : nullptr, B, (float)PSVD_MIXED_CORR_MAX,
+            (float)PSVD_MIXED_RECON_MAX, w.mflag, w.any + 1, info);
+        count_launch(1);
     }
     return cudaGetLastError() == cudaSuccess ? PSVD_OK : PSVD_ERR_CUDA;
 }
@@ -563,8 +584,8 @@ static psvd_opts svd_resolve(const psvd_opts *p) {
     return o;
 }
 
-// The FP32-accurate rerun of the matrices the mixed pass flagged: options of the
-// plain conservative path, and the workspace layout (gathered inputs, outputs, records,
+// The FP32-accurate rerun of the matrices the first pass flagged (a mixed result that failed
+// its checks, or a learned schedule that missed tol): options of the plain conservative path, and the workspace layout (gathered inputs, outputs, records,
 // index list, then the plain pipeline's own workspace), carved from the start of the
 // same workspace once the mixed pass has finished with it.
 static psvd_opts plain_opts(const psvd_opts &o) {
@@ -578,7 +599,7 @@ static psvd_opts plain_opts(const psvd_opts &o) {
 struct RerunWS {
     float *A = nullptr, *U = nullptr, *S = nullptr, *VT = nullptr;
     psvd_info *info = nullptr;
-    int *idx = nullptr;
+    int *idx = nullptr, *why = nullptr;   // rerun matrix j is batch entry idx[j], for reasons why[j]
     SvdWS w;
     template <class C>
     void carve(C &cv, int F, int m, int n, const psvd_opts &plain) {
@@ -589,18 +610,19 @@ struct RerunWS {
         VT = cv.template take<float>(F64 * n * n);
         info = cv.template take<psvd_info>(F64);
         idx = cv.template take<int>(F64);
+        why = cv.template take<int>(F64);
         w.carve(cv, F, m, n, plain);
     }
 };
 
-static int mixed_fallback(const float *A, float *U, float *S, float *VT, int B, int m, int n, const SvdWS &w,
-                          const psvd_opts &o, void *ws, size_t ws_bytes, psvd_info *info, cudaStream_t st) {
+static int rerun_flagged(const float *A, float *U, float *S, float *VT, int B, int m, int n, const SvdWS &w,
+                         const psvd_opts &o, void *ws, size_t ws_bytes, psvd_info *info, cudaStream_t st) {
     std::vector<int> flags(B);
     PSVD_TRY(cudaMemcpyAsync(flags.data(), w.mflag, sizeof(int) * (size_t)B, cudaMemcpyDeviceToHost, st));
     PSVD_TRY(cudaStreamSynchronize(st));
-    std::vector<int> idx;
+    std::vector<int> idx, why;
     for (int b = 0; b < B; ++b)
-        if (flags[b]) idx.push_back(b);
+        if (flags[b]) { idx.push_back(b); why.push_back(flags[b]); }
     const int F = (int)idx.size();
     if (F == 0) return PSVD_OK;
     const psvd_opts po = plain_opts(o);
@@ -610,6 +632,7 @@ static int mixed_fallback(const float *A, float *U, float *S, float *VT, int B, 
     if (cv.overflow) return PSVD_ERR_WORKSPACE;
     const size_t mn = (size_t)m * n, nn = (size_t)n * n;
     PSVD_TRY(cudaMemcpyAsync(r.idx, idx.data(), sizeof(int) * (size_t)F, cudaMemcpyHostToDevice, st));
+    PSVD_TRY(cudaMemcpyAsync(r.why, why.data(), sizeof(int) * (size_t)F, cudaMemcpyHostToDevice, st));
     for (int j = 0; j < F; ++j)
         PSVD_TRY(cudaMemcpyAsync(r.A + j * mn, A + idx[j] * mn, sizeof(float) * mn, cudaMemcpyDeviceToDevice, st));
     PSVD_TRY_RC(svd_forward(r.A, r.U, r.S, r.VT, r.w, po, info ? r.info : nullptr, st));
@@ -620,7 +643,7 @@ static int mixed_fallback(const float *A, float *U, float *S, float *VT, int B, 
         PSVD_TRY(cudaMemcpyAsync(VT + b * nn, r.VT + j * nn, sizeof(float) * nn, cudaMemcpyDeviceToDevice, st));
     }
     if (info) {
-        info_scatter_kernel<<<(F + 127) / 128, 128, 0, st>>>(info, r.info, r.idx, F);
+        info_scatter_kernel<<<(F + 127) / 128, 128, 0, st>>>(info, r.info, r.idx, r.why, F);
         count_launch(1);
         PSVD_TRY(cudaGetLastError());
     }
@@ -634,7 +657,7 @@ extern "C" size_t psvd_svd_workspace_bytes(int64_t batch, int64_t m, int64_t n, 
     SvdWS w;
     w.carve(s, (int)batch, (int)m, (int)n, o);
     size_t need = s.used;
-    if (o.precision != PSVD_PREC_FP32) {
+    if (o.precision != PSVD_PREC_FP32 || o.schedule == PSVD_SCHED_LEARNED) {
         // room for rerunning every matrix on the FP32-accurate path
         Sizer s2;
         RerunWS r;
@@ -652,7 +675,8 @@ extern "C" int psvd_svd_fwd(const float *A, float *U, float *S, float *VT, int64
         return PSVD_ERR_ARG;
     if (o.precision != PSVD_PREC_FP32 && o.precision != PSVD_PREC_MIXED && o.precision != PSVD_PREC_MIXED_BF16)
         return PSVD_ERR_ARG;
-    if (o.schedule == PSVD_SCHED_LEARNED && !o.lower_bound) return PSVD_ERR_ARG;
+    if (o.schedule < PSVD_SCHED_CANS || o.schedule > PSVD_SCHED_PE) return PSVD_ERR_ARG;
+    if ((o.schedule == PSVD_SCHED_LEARNED || o.schedule == PSVD_SCHED_PE) && !o.lower_bound) return PSVD_ERR_ARG;
     if (int e = check_device()) return e;
     if (ws_bytes < psvd_svd_workspace_bytes(batch, m, n, &o)) return PSVD_ERR_WORKSPACE;
     Carver cv(ws, ws_bytes);
@@ -661,8 +685,9 @@ extern "C" int psvd_svd_fwd(const float *A, float *U, float *S, float *VT, int64
     if (cv.overflow) return PSVD_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     PSVD_TRY_RC(svd_forward(A, U, S, VT, w, o, info, st));
-    // mixed precision: the one host synchronization of this call (reads which matrices the
-    // checks flagged for the FP32-accurate rerun)
-    if (w.mixed) return mixed_fallback(A, U, S, VT, (int)batch, (int)m, (int)n, w, o, ws, ws_bytes, info, st);
+    // mixed precision or the learned schedule: the one host synchronization of this call
+    // (reads which matrices need the rerun on the plain path)
+    if (w.mixed || w.learned)
+        return rerun_flagged(A, U, S, VT, (int)batch, (int)m, (int)n, w, o, ws, ws_bytes, info, st);
     return PSVD_OK;
 }

@@ -2,12 +2,13 @@
 learning of Section 5's compression experiment, Dobi-SVD style), on synthetic activations.
 
     python -m paper_2609_32505_gb300.rank_demo [--layers 4] [--d 256] [--tokens 1024]
-                                               [--ratio 0.4] [--eps 0.1 1 10] [--iters 150]
+                                               [--ratio 0.35] [--eps 0.1 1 10] [--iters 150]
 
 A small synthetic network stands in for the language model (whose weights and data are not
-available): L linear layers of width d with seeded weights of power-law spectrum, a seeded
-input of `tokens` rows with a decaying spectrum, and tanh between layers.  Each layer i has
-a trainable continuous rank gamma_i.  At every step the activations A_i = H_{i-1} W_i^T are
+available): L residual blocks h <- h + tanh(h W_i^T) of width d, with seeded weights whose
+spectra have a knee at a layer-specific rank (the layers differ in how compressible their
+activations are, as the layers of a real model do) and a seeded full-rank input of `tokens`
+rows.  Each layer i has a trainable continuous rank gamma_i.  At every step the activations A_i = H_{i-1} W_i^T are
 factored by the library (psvd.svd, forward Algorithm 1 and backward Algorithm 4 with the
 chosen eps), truncated softly -- A_i ~ U diag(sigma o m(gamma_i)) V^T with
 m_j(gamma) = sigmoid((gamma - j) / tau) -- and passed on; the loss is the relative distance
@@ -40,15 +41,21 @@ import paper_2609_32505_gb300 as P  # noqa: E402
 import workloads as W  # noqa: E402
 
 
+# knee position of each layer's weight spectrum, as a fraction of d (cycled over the layers)
+KNEES = (12 / 128, 80 / 128, 32 / 128, 56 / 128)
+
+
 def make_problem(layers: int, d: int, tokens: int, seed: int = 0, device="cuda"):
-    """Seeded weights (power-law spectra, decay varying by layer) and input activations."""
+    """Seeded weights and input.  Weight i: s_j = 1 - j / (2 r_i) up to its knee r_i, then
+    0.5 exp(-(j - r_i) / 4); input: s_j = 0.5 sqrt(tokens) exp(-2 j / d) (full rank)."""
     ws = []
+    j = np.arange(d, dtype=np.float64)
     for i in range(layers):
-        p = 0.4 + 0.5 * i / max(1, layers - 1)               # later layers: faster decay
-        s = (np.arange(1, d + 1, dtype=np.float64) ** -p) * math.sqrt(d)
+        r = max(1, int(round(KNEES[i % len(KNEES)] * d)))
+        s = np.where(j < r, 1.0 - 0.5 * j / r, 0.5 * np.exp(-(j - r) / 4.0))
         a, _, _ = W.constructed(seed * 100 + i, d, d, s)
-        ws.append(torch.from_numpy((a / np.linalg.norm(a, 2)).astype(np.float32)).to(device))
-    sx = np.exp(-np.arange(d, dtype=np.float64) / (d / 6.0)) * 10.0
+        ws.append(torch.from_numpy(a.astype(np.float32)).to(device))
+    sx = np.exp(-2.0 * j / d) * math.sqrt(tokens) * 0.5
     x, _, _ = W.constructed(seed * 100 + 99, tokens, d, sx)
     return ws, torch.from_numpy(x.astype(np.float32)).to(device)
 
@@ -74,7 +81,7 @@ def forward(ws, x, gammas=None, ranks=None, eps=1e-8, kreg_mode=0, tau=2.0):
                 keep[:int(ranks[i])] = 1.0
                 s = s * keep
             a = (u * s[None, :]) @ vt
-        h = torch.tanh(a)
+        h = h + torch.tanh(a)
     return h
 
 
@@ -89,7 +96,7 @@ def demo_loss(ws, x, ref, gammas, ratio, lam, eps, kreg_mode, tau=2.0):
     return rel_err(y, ref) ** 2 + lam * (kept - ratio) ** 2, y
 
 
-def train(ws, x, ratio: float, eps: float, kreg_mode: int = 0, iters: int = 150, lr: float = 2.0,
+def train(ws, x, ratio: float, eps: float, kreg_mode: int = 0, iters: int = 150, lr: float = 1.0,
           lam: float = 50.0, tau: float = 2.0):
     d = ws[0].shape[0]
     ref = forward(ws, x)
@@ -111,7 +118,7 @@ def train(ws, x, ratio: float, eps: float, kreg_mode: int = 0, iters: int = 150,
             for gm in gammas:
                 gm.clamp_(1.0, float(d))
         if it % 10 == 0 or it == iters - 1:
-            curve.append(float(loss))
+            curve.append(float(loss.detach()))
     torch.cuda.synchronize()
     sec = (time.perf_counter() - t0) / iters
     return [float(gm) for gm in gammas], curve, grad_norms, sec
@@ -126,7 +133,7 @@ def hard_ranks(gammas, total: int, d: int):
     return np.clip(r, 1, d)
 
 
-def run(layers=4, d=256, tokens=1024, ratio=0.4, eps_list=(0.1, 1.0, 10.0), iters=150, kreg_mode=0, seed=0):
+def run(layers=4, d=256, tokens=1024, ratio=0.35, eps_list=(0.1, 1.0, 10.0), iters=150, kreg_mode=0, seed=0):
     ws, x = make_problem(layers, d, tokens, seed)
     ref = forward(ws, x)
     total = int(round(ratio * d * layers))
@@ -150,7 +157,7 @@ def main(argv=None):
     ap.add_argument("--layers", type=int, default=4)
     ap.add_argument("--d", type=int, default=256)
     ap.add_argument("--tokens", type=int, default=1024)
-    ap.add_argument("--ratio", type=float, default=0.4)
+    ap.add_argument("--ratio", type=float, default=0.35)
     ap.add_argument("--eps", type=float, nargs="+", default=[0.1, 1.0, 10.0])
     ap.add_argument("--iters", type=int, default=150)
     ap.add_argument("--kreg", type=int, default=0)

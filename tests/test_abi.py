@@ -95,10 +95,24 @@ def test_python_mirrors_of_header_constants():
     d, fields = _header()
     assert (P.PREC_FP32, P.PREC_MIXED, P.PREC_MIXED_BF16) == (d["PSVD_PREC_FP32"], d["PSVD_PREC_MIXED"],
                                                               d["PSVD_PREC_MIXED_BF16"])
-    assert (P.SCHED_CANS, P.SCHED_LEARNED, P.SCHED_NS) == (d["PSVD_SCHED_CANS"], d["PSVD_SCHED_LEARNED"],
-                                                           d["PSVD_SCHED_NS"])
+    assert (P.SCHED_CANS, P.SCHED_LEARNED, P.SCHED_NS, P.SCHED_PE) == (
+        d["PSVD_SCHED_CANS"], d["PSVD_SCHED_LEARNED"], d["PSVD_SCHED_NS"], d["PSVD_SCHED_PE"])
     assert P.MIXED_CORR_MAX == d["PSVD_MIXED_CORR_MAX"]
     assert P.MIXED_RECON_MAX == d["PSVD_MIXED_RECON_MAX"]
     assert P.MIXED_LB_MIN == d["PSVD_MIXED_LB_MIN"]
     assert [name for _, name in fields] == P.INFO_FIELDS
     assert [t for t, _ in fields] == ["int"] * P.INFO_INTS + ["float"] * (P.INFO_WORDS - P.INFO_INTS)
+
+
+def test_python_opts_mirror_header_struct():
+    # the binding's ctypes psvd_opts: same fields, same order, same C types as the header
+    import paper_2609_32505_gb300 as P
+    txt = open(os.path.join(ROOT, "include", "psvd.h")).read()
+    body = re.search(r"typedef struct psvd_opts \{(.*?)\} psvd_opts;", txt, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(int|double|const float)\s*(\*?)\s*([a-z0-9_]+)\s*;", body)
+    names = [n for _, _, n in fields]
+    assert names == [f for f, _ in P.Opts._fields_]
+    kinds = {"int": ctypes.c_int, "double": ctypes.c_double}
+    for (t, star, name), (fname, ct) in zip(fields, P.Opts._fields_):
+        assert ct is (ctypes.c_void_p if star else kinds[t]), name

@@ -21,7 +21,7 @@ def _np_forward(ws, x, gammas, tau):
         u, s, vt, _ = O.svd(a)
         d = s.shape[0]
         m = 1.0 / (1.0 + np.exp(-(g - np.arange(d)) / tau))
-        h = np.tanh((u * (s * m)[None, :]) @ vt)
+        h = h + np.tanh((u * (s * m)[None, :]) @ vt)
     return h
 
 
@@ -58,10 +58,20 @@ def test_rank_gradient_matches_fp64_finite_differences():
 
 @pytest.mark.parametrize("eps", [0.1, 1.0, 10.0])
 def test_rank_demo_trains(eps):
+    # the layers' knees differ, so the learned allocation must beat the uniform one of the same
+    # total rank (hard truncation of both), and the loss must fall
     from paper_2609_32505_gb300 import rank_demo as R
-    ws, x = R.make_problem(3, 64, 256, seed=1)
-    gam, curve, gn, sec = R.train(ws, x, ratio=0.4, eps=eps, iters=30)
+    layers, d, ratio = 4, 128, 0.35
+    ws, x = R.make_problem(layers, d, 512, seed=0)
+    gam, curve, gn, sec = R.train(ws, x, ratio=ratio, eps=eps, iters=120)
     assert all(math.isfinite(g) for g in gam) and all(math.isfinite(g) for g in gn)
-    assert curve[-1] < curve[0]
-    ranks = R.hard_ranks(gam, int(round(0.4 * 64 * 3)), 64)
-    assert ranks.sum() == int(round(0.4 * 64 * 3))
+    assert curve[-1] < 0.5 * curve[0]
+    total = int(round(ratio * d * layers))
+    ranks = R.hard_ranks(gam, total, d)
+    assert ranks.sum() == total
+    uniform = [total // layers + (1 if i < total % layers else 0) for i in range(layers)]
+    ref = R.forward(ws, x)
+    with torch.no_grad():
+        e_l = float(R.rel_err(R.forward(ws, x, ranks=ranks), ref))
+        e_u = float(R.rel_err(R.forward(ws, x, ranks=uniform), ref))
+    assert e_l < 0.7 * e_u, (ranks, e_l, e_u)

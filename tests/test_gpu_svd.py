@@ -195,3 +195,33 @@ def test_mixed_learned_gate_on_small_lower_bound():
     u, s, vt = U.cpu().double().numpy(), S.cpu().double().numpy(), VT.cpu().double().numpy()
     for b, a in enumerate(mats):
         _gates(a, u[b], s[b], vt[b], O.svd(a)[1], 1)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_learned_schedule_miss_is_recomputed_on_the_plain_path(precision):
+    # svd_fwd with the learned schedule and a deliberately over-predicted bound for the first
+    # matrix: that matrix misses tol within its budget, and instead of a conservative rerun of
+    # the polar iteration inside the call (as psvd_polar_fwd does) it joins the one recompute
+    # of flagged matrices on the plain FP32-accurate path; the record says why.
+    import paper_2609_32505_gb300 as P
+    n = 200
+    mats = [W.constructed(31 + k, n, n, W.kappa_spectrum(n, k_))[0].astype(np.float32).astype(np.float64)
+            for k, k_ in enumerate((1e3, 10.0))]
+    lbs = []
+    for a in mats:
+        scale = np.sqrt(np.abs(a).sum(0).max() * np.abs(a).sum(1).max())
+        lbs.append(0.5 * O.svd(a)[1][-1] / scale)
+    lbs[0] = 0.9                                            # far above sigma_min(X0)
+    A = torch.from_numpy(np.stack(mats).astype(np.float32)).cuda()
+    lb = torch.tensor(lbs, dtype=torch.float32, device="cuda")
+    U, S, VT, info = P.svd_fwd(A, P.make_opts(precision=precision, schedule=P.SCHED_LEARNED, lower_bound=lb,
+                                              budget=4), return_info=True)
+    torch.cuda.synchronize()
+    assert info[0]["sched_fallback"] == 1 and info[0]["status"] == 0
+    assert info[0]["steps_3xtf32"] > 0 and info[0]["qr_fallback"] == 0
+    assert info[1]["sched_fallback"] == 0
+    if precision:
+        _fallback_consistent(info)
+    u, s, vt = U.cpu().double().numpy(), S.cpu().double().numpy(), VT.cpu().double().numpy()
+    for b, a in enumerate(mats):
+        _gates(a, u[b], s[b], vt[b], O.svd(a)[1], precision)
