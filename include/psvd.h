@@ -61,13 +61,16 @@ extern "C" {
 #define PSVD_SCHED_CANS     0 /* conservative CANS: preprocessing for [t,1] then greedy
                                  optimal cubics from [1-delta, 1+delta] (Appendix B.8)     */
 #define PSVD_SCHED_LEARNED  1 /* greedy optimal cubics from [l_b, 1], l_b a predicted lower
-                                 bound of sigma_min(X0) per matrix (opts.lower_bound)       */
+                                 bound of sigma_min(X0) per matrix (opts.lower_bound), each
+                                 applied to x / 1.01 while the interval is wider than 1e-2
+                                 (undamped, they lose accuracy from small bounds: ~2e-4
+                                 relative reconstruction at kappa = 1e6)                     */
 #define PSVD_SCHED_NS       2 /* classical Newton-Schulz, p(x) = 1.5 x - 0.5 x^3           */
 #define PSVD_SCHED_PE       3 /* comparison schedule of the polar-iteration ablation (Appendix B),
-                                 Polar-Express style: the greedy optimal cubics of schedule 1
-                                 from [l_b, 1] (opts.lower_bound), each applied to x / 1.01 while
-                                 the tracked interval is wider than 1e-2, then undamped.  No
-                                 conservative rerun.                                          */
+                                 Polar-Express style: the greedy optimal cubics from [l_b, 1]
+                                 (opts.lower_bound), each applied to x / 1.01 until that stops
+                                 shrinking the interval (the damped fixed point, ~1.5e-4 from
+                                 1), then undamped.  No budget, no conservative rerun.        */
 
 typedef struct psvd_opts {
     int    precision;     /* PSVD_PREC_*                                        default 0    */
@@ -82,8 +85,15 @@ typedef struct psvd_opts {
                              (0 = automatic: predicted steps + 5)                           */
     double *res_history;  /* DEVICE [(max_iter + pre_iters + 1) x batch] or NULL: entry
                              k * batch + b receives ||X_k^T X_k - I||_F / sqrt(n) at step k
-                             of matrix b (0 once it has finished; for schedule 1 the steps of
-                             the last pass, i.e. of the conservative rerun where there was one) */
+                             of matrix b (0 once it has finished; psvd_polar_fwd with schedule
+                             1: the conservative rerun's steps for the matrices it reran)     */
+    int    preqr;         /* 1: for m > n, factor M = Q R first (blocked Householder QR on the
+                             GPU, psvd_qr), run the method on the n x n factor R and return
+                             U = Q U_R (svd_fwd) or W = Q W_R, H = H_R (polar_fwd) -- the QR
+                             preprocessing of rectangular inputs of Section 4.1.  A learned
+                             schedule's lower bounds then refer to R.  0 (default): the
+                             method runs on M itself.  Needs m <= 23040; psvd_polar_fwd_noalloc
+                             rejects it.                                                      */
 } psvd_opts;
 
 /* Fills *o with the defaults above (host pointer). */
@@ -251,6 +261,16 @@ int psvd_mlp_train_step(float *params, float *grads, float *m1, float *m2, const
 /* psvd_mlp_grad -- loss and gradients only (no parameter update). */
 int psvd_mlp_grad(const float *params, const float *F, const float *target, int64_t nb,
                   float *grads, float *loss, void *stream);
+
+/* ---- QR (Appendix A.2's fallback; Section 4.1's preprocessing) ------------------
+ * psvd_qr -- thin QR A = Q R of a batch of m x n matrices (m >= n), diag(R) >= 0, by blocked
+ *   Householder: panels of 64 (or 32) columns factored by one thread-block cluster per
+ *   matrix, trailing updates and the accumulation of Q in compact-WY form on the split-TF32
+ *   tcgen05 product kernel.  A: batch x m x n (read); Q: batch x m x n out (may alias A);
+ *   R: batch x n x n out, upper triangular (may be NULL).  m <= 23040. */
+size_t psvd_qr_workspace_bytes(int64_t batch, int64_t m, int64_t n);
+int psvd_qr(const float *A, float *Q, float *R, int64_t batch, int64_t m, int64_t n, void *ws,
+            size_t ws_bytes, void *stream);
 
 /* ---- building block ------------------------------------------------------------
  * psvd_gemm_tn -- D[b] = A[b] B[b]^T for A: batch x M x K, B: batch x N x K, D: batch x M x N

@@ -36,7 +36,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("schedule", ctypes.c_int), ("delta", ctypes.c_double),
                 ("pre_iters", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
                 ("eps_qr", ctypes.c_double), ("lower_bound", ctypes.c_void_p), ("budget", ctypes.c_int),
-                ("res_history", ctypes.c_void_p)]
+                ("res_history", ctypes.c_void_p), ("preqr", ctypes.c_int)]
 
 
 INFO_FIELDS = ["status", "iters", "qr_fallback", "sched_fallback", "prec_fallback", "steps_bf16", "steps_tf32",
@@ -83,6 +83,8 @@ def lib():
         "psvd_polar_bwd": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, i64, i64, i64, ctypes.c_double, vp, sz, vp]),
         "psvd_eigh_bwd_workspace_bytes": (sz, [i64, i64]),
         "psvd_eigh_bwd": (ctypes.c_int, [vp, vp, vp, vp, vp, i64, i64, ctypes.c_double, ctypes.c_int, vp, sz, vp]),
+        "psvd_qr_workspace_bytes": (sz, [i64, i64, i64]),
+        "psvd_qr": (ctypes.c_int, [vp, vp, vp, i64, i64, i64, vp, sz, vp]),
         "psvd_profile_enable": (ctypes.c_int, [ctypes.c_int]),
         "psvd_sketch_workspace_bytes": (sz, [i64, i64, i64, i64]),
         "psvd_sketch_features": (ctypes.c_int, [vp, vp, i64, vp, i64, i64, i64, vp, sz, vp]),
@@ -142,13 +144,14 @@ def gemm_tn(a: torch.Tensor, b: torch.Tensor, precision: int = GEMM_TF32X3) -> t
 
 def make_opts(precision: int = PREC_FP32, schedule: int = SCHED_CANS, delta: float = 0.99, pre_iters: int = 2,
               max_iter: int = 50, tol: float = 1e-5, eps_qr: float = 1e-5, lower_bound=None, budget: int = 0,
-              res_history=None):
+              res_history=None, preqr: int = 0):
     o = Opts()
     lib().psvd_default_opts(ctypes.byref(o))
     o.precision, o.schedule, o.delta, o.pre_iters = precision, schedule, delta, pre_iters
     o.max_iter, o.tol, o.eps_qr, o.budget = max_iter, tol, eps_qr, budget
     o.lower_bound = None if lower_bound is None else lower_bound.data_ptr()
     o.res_history = None if res_history is None else res_history.data_ptr()
+    o.preqr = int(preqr)
     return o
 
 
@@ -180,6 +183,20 @@ def polar(a: torch.Tensor, opts: Opts | None = None, want_h: bool = True, return
                             _ptr(info), _stream()), "psvd_polar_fwd")
     out = (W[0] if sq else W, None if H is None else (H[0] if sq else H))
     return out + (info_dict(info),) if return_info else out
+
+
+def qr(a: torch.Tensor, want_r: bool = True):
+    """Thin QR A = Q R with diag(R) >= 0 (batch of m x n, m >= n) on the GPU (psvd_qr)."""
+    A, sq = _batched(a.contiguous().float())
+    bt, m, n = A.shape
+    Q = torch.empty_like(A)
+    R = torch.empty(bt, n, n, device=A.device, dtype=torch.float32) if want_r else None
+    L = lib()
+    ws = _workspace(L.psvd_qr_workspace_bytes(bt, m, n), A.device)
+    _check(L.psvd_qr(_ptr(A), _ptr(Q), _ptr(R), bt, m, n, _ptr(ws), ws.numel(), _stream()), "psvd_qr")
+    if sq:
+        return Q[0], None if R is None else R[0]
+    return Q, R
 
 
 def eigh(h: torch.Tensor):

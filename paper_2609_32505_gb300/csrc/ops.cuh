@@ -82,6 +82,48 @@ struct EpiStore {
     PSVD_DEV void finish(Acc &, int, int, int) const {}
 };
 
+// In place: X[r][c] -= acc for a matrix kept split in TF32 hi/lo halves (the eigensolver's
+// back-transform, the QR's trailing updates); the reads of a chunk are issued before its
+// stores (pre / elem_pre).
+struct EpiSubSplit {
+    int rows, cols;
+    float *hi, *lo;
+    long long ld, bs;
+    struct Acc {};
+    static constexpr bool kElem = true, kPre = true;
+    PSVD_DEV bool staged() const { return true; }
+    PSVD_DEV float pre(int b, int r, int c) const {
+        if (r >= rows || c >= cols) return 0.f;
+        const long long o = b * bs + (long long)r * ld + c;
+        return hi[o] + lo[o];
+    }
+    PSVD_DEV void elem_pre(Acc &, int b, int r, int c, float v, float p) const {
+        if (r >= rows || c >= cols) return;
+        const long long o = b * bs + (long long)r * ld + c;
+        float h, l;
+        split_tf32(p - v, h, l);
+        hi[o] = h;
+        lo[o] = l;
+    }
+    PSVD_DEV void elem(Acc &a, int b, int r, int c, float v) const { elem_pre(a, b, r, c, v, pre(b, r, c)); }
+    PSVD_DEV void begin(Acc &) const {}
+    PSVD_DEV void chunk(Acc &, int b, int r, int c0, int, int, float (&v)[16]) const {
+        if (r >= rows) return;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int c = c0 + i;
+            if (c >= cols) break;
+            const long long o = b * bs + (long long)r * ld + c;
+            const float x = (hi[o] + lo[o]) - v[i];
+            float h, l;
+            split_tf32(x, h, l);
+            hi[o] = h;
+            lo[o] = l;
+        }
+    }
+    PSVD_DEV void finish(Acc &, int, int, int) const {}
+};
+
 inline EpiStore epi_store_plain(float *out, long long ld, long long bs, int rows, int cols) {
     EpiStore e;
     memset(&e, 0, sizeof(e));

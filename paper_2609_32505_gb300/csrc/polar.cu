@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "polar.cuh"
+#include "qr.cuh"
 #include "schedule.h"
 
 namespace psvd {
@@ -101,37 +102,46 @@ struct CoefTable {
     float c1[72], c3[72];
 };
 
-// coef[(k * B + b) * 2 + {0,1}] for k < K.  Learned: greedy optimal cubics from
-// [l_b, 1] per matrix (FP64), and the step budget before the conservative rerun; with
-// gate_x3, a matrix whose bound is below PSVD_MIXED_LB_MIN starts on the split-TF32 rung.
-// Damped (the Polar-Express-style comparison schedule): the same greedy cubics from [l_b, 1]
-// applied to x / kPeDamp while the tracked interval is wider than kPeWidth, then undamped
-// from the interval reached; no budget (the comparison schedule has no fallback).
+// coef[(k * B + b) * 2 + {0,1}] for k < K.  Learned: greedy optimal cubics from [l_b, 1] per
+// matrix (FP64), each applied to x / kPeDamp while the tracked interval is wider than
+// kPeWidth (undamped greedy cubics from a small bound lose accuracy: relative
+// reconstruction ~2e-4 at kappa = 1e6 in FP32 against ~3e-6 damped, for the same number of
+// steps), and the step budget before the conservative rerun; with gate_x3, a matrix whose
+// bound is below PSVD_MIXED_LB_MIN starts on the split-TF32 rung.
+// Damped (schedule PSVD_SCHED_PE, the Polar-Express-style comparison): the same damped cubics
+// from [l_b, 1] until a damped step stops shrinking the interval (width below 0.1 and less
+// than 10% gained: the damped fixed point near 1 - 1.5e-4, the plateau the ablation
+// describes), then undamped from there; no budget and no rerun.
 constexpr double kPeDamp = 1.01, kPeWidth = 1e-2;
 __global__ void schedule_fill_kernel(int B, int K, CoefTable tab, const float *lower, int learned, double tol,
                                      int budget_opt, const int *active, float *coef, int *budget, int gate_x3,
-                                     int *prec, int damped = 0) {
+                                     int *prec, int pe = 0) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     if (active && !active[b]) return;
-    if (damped) {
+    if (learned || pe) {
         double l = (double)lower[b];
+        if (learned && gate_x3 && !(l >= PSVD_MIXED_LB_MIN)) prec[b] = PREC_TF32X3;
         if (!(l > 1e-12)) l = 1e-12;
         if (l > 0.999) l = 0.999;
         double lo = l, hi = 1.0;
         bool damping = true;
         for (int k = 0; k < K; ++k) {
-            if (damping && fmax(1.0 - lo, hi - 1.0) <= kPeWidth) damping = false;
+            const double width = fmax(1.0 - lo, hi - 1.0);
             double nlo, nhi;
             Cubic c;
-            if (damping) c = damped_cubic(lo, hi, kPeDamp, &nlo, &nhi);
-            else { c = cans_cubic(lo, hi); nlo = 1.0 - c.e; nhi = 1.0 + c.e; }
+            if (damping) {
+                c = damped_cubic(lo, hi, kPeDamp, &nlo, &nhi);
+                const double nw = fmax(1.0 - nlo, nhi - 1.0);
+                if (learned ? width <= kPeWidth : (width < 0.1 && nw > 0.9 * width)) damping = false;
+            }
+            if (!damping) { c = cans_cubic(lo, hi); nlo = 1.0 - c.e; nhi = 1.0 + c.e; }
             coef[((long long)k * B + b) * 2 + 0] = (float)c.c1;
             coef[((long long)k * B + b) * 2 + 1] = (float)c.c3;
             lo = nlo;
             hi = nhi;
         }
-        budget[b] = K;
+        budget[b] = learned ? (budget_opt > 0 ? budget_opt : greedy_steps_to(l, 0.5 * tol, K) + 5) : K;
         return;
     }
     if (!learned) {
@@ -143,19 +153,6 @@ __global__ void schedule_fill_kernel(int B, int K, CoefTable tab, const float *l
         budget[b] = K;
         return;
     }
-    double l = (double)lower[b];
-    if (gate_x3 && !(l >= PSVD_MIXED_LB_MIN)) prec[b] = PREC_TF32X3;
-    if (!(l > 1e-12)) l = 1e-12;
-    if (l > 0.999) l = 0.999;
-    double lo = l, hi = 1.0;
-    for (int k = 0; k < K; ++k) {
-        Cubic c = cans_cubic(lo, hi);
-        coef[((long long)k * B + b) * 2 + 0] = (float)c.c1;
-        coef[((long long)k * B + b) * 2 + 1] = (float)c.c3;
-        lo = 1.0 - c.e;
-        hi = 1.0 + c.e;
-    }
-    budget[b] = budget_opt > 0 ? budget_opt : greedy_steps_to(l, 0.5 * tol, K) + 5;
 }
 
 // ------------------------------------------------------------ step epilogues
@@ -347,10 +344,12 @@ __global__ void symmetrize_kernel(const float *Hraw, int n, float *Hsym, float *
 }
 
 // hist[k * B + b] = ||G_k - I||_F / sqrt(n) at the Gram of step k (0 where the matrix had
-// already finished, or the step was never reached).
-__global__ void res_history_kernel(const double *res, int K, int B, int n, double *hist) {
+// already finished, or the step was never reached), for the matrices with only[b] != 0
+// (all when only is null).
+__global__ void res_history_kernel(const double *res, int K, int B, int n, const int *only, double *hist) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= K * B) return;
+    if (only && !only[t % B]) return;
     hist[t] = sqrt(res[t] / (double)n);
 }
 
@@ -524,6 +523,11 @@ int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &
     if (learned) kmax = std::min(w.kcap, o.budget > 0 ? o.budget : greedy_steps_to(1e-12, 0.5 * o.tol, w.kcap + 1) + 5);
     if (int rc = run_iteration(w, kmax, o.tol, learned, w.fres, nullptr, st)) return rc;
     if (learned && rerun_learned) {
+        if (o.res_history) {        // the learned pass's history; the rerun overwrites its own matrices'
+            const int K = w.kcap + 1;
+            res_history_kernel<<<(K * B + 127) / 128, 128, 0, st>>>(w.res, K, B, n, nullptr, o.res_history);
+            count_launch(1);
+        }
         // Matrices whose learned schedule missed tol within budget are rerun from X0 with the
         // conservative schedule.  Nothing is read back: the rerun's steps are launched for the
         // whole budget, gated on the number of rerun matrices (misc[0]) and then on the
@@ -543,6 +547,11 @@ int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &
             return PSVD_ERR_CUDA;
         if (int rc = prepare_x0(A, w, st, w.done)) return rc;
         if (int rc = run_iteration(w, w.kcap, o.tol, false, w.fres, w.misc, st)) return rc;
+        if (o.res_history) {
+            const int K = w.kcap + 1;
+            res_history_kernel<<<(K * B + 127) / 128, 128, 0, st>>>(w.res, K, B, n, w.fallback, o.res_history);
+            count_launch(1);
+        }
         set_all_done_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, w.done);
         count_launch(1);
     }
@@ -571,9 +580,9 @@ int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &
                                                            info);
         count_launch(1);
     }
-    if (o.res_history) {
+    if (o.res_history && !(learned && rerun_learned)) {
         const int K = w.kcap + 1;
-        res_history_kernel<<<(K * B + 127) / 128, 128, 0, st>>>(w.res, K, B, n, o.res_history);
+        res_history_kernel<<<(K * B + 127) / 128, 128, 0, st>>>(w.res, K, B, n, nullptr, o.res_history);
         count_launch(1);
     }
     return cudaGetLastError() == cudaSuccess ? PSVD_OK : PSVD_ERR_CUDA;
@@ -588,7 +597,7 @@ static bool opts_ok(const psvd_opts &o) {
     return (o.precision == PSVD_PREC_FP32 || o.precision == PSVD_PREC_MIXED || o.precision == PSVD_PREC_MIXED_BF16) &&
            (o.schedule >= PSVD_SCHED_CANS && o.schedule <= PSVD_SCHED_PE) && o.delta > 0 && o.delta < 1 &&
            o.pre_iters >= 0 && o.pre_iters <= 8 && o.max_iter >= 1 && o.max_iter <= 64 && o.tol > 0 &&
-           o.eps_qr > 0 &&
+           o.eps_qr > 0 && (o.preqr == 0 || o.preqr == 1) &&
            ((o.schedule != PSVD_SCHED_LEARNED && o.schedule != PSVD_SCHED_PE) || o.lower_bound != nullptr);
 }
 
@@ -599,13 +608,51 @@ static psvd_opts resolve_opts(const psvd_opts *p) {
     return o;
 }
 
-extern "C" size_t psvd_polar_workspace_bytes(int64_t batch, int64_t m, int64_t n, const psvd_opts *opts) {
-    psvd_opts o = resolve_opts(opts);
-    if (batch <= 0 || m <= 0 || n <= 0) return 0;
+static size_t polar_direct_bytes(int64_t batch, int64_t m, int64_t n, const psvd_opts &o) {
     Sizer s;
     PolarWS w;
     w.carve(s, (int)batch, (int)m, (int)n, polar_kcap(o), o.precision);
     return s.used + 256;
+}
+
+// QR preprocessing (Section 4.1, rectangular matrices): M = Q R, polar decomposition of R,
+// W = Q W_R, H = H_R.  Layout: Q, R, W_R, then one region shared in turn by the QR, the
+// iteration on R and the operands of the final product.
+struct PolarPreqr {
+    float *Q = nullptr, *R = nullptr, *WR = nullptr;
+    char *rest = nullptr;
+    size_t rest_bytes = 0, need = 0;
+    void plan(void *ws, size_t ws_bytes, int64_t B, int64_t m, int64_t n, const psvd_opts &o) {
+        Carver cv(ws, ws_bytes);
+        Q = cv.take<float>(B * m * n);
+        R = cv.take<float>(B * n * n);
+        WR = cv.take<float>(B * n * n);
+        const size_t head = (size_t)round_up((long long)cv.used, 256);
+        Sizer q;
+        QrWS qw;
+        qw.carve(q, (int)B, (int)m, (int)n);
+        const long long ld = pad_ld(n);
+        const size_t ops = (size_t)(2 * B * m * ld + 2 * B * n * ld) * sizeof(float) + 1024;
+        need = head + std::max(std::max(q.used + 256, polar_direct_bytes(B, n, n, o)), ops);
+        rest = ws ? static_cast<char *>(ws) + head : nullptr;
+        rest_bytes = ws_bytes > head ? ws_bytes - head : 0;
+    }
+};
+
+static bool polar_use_preqr(const psvd_opts &o, int64_t m, int64_t n) {
+    int nb = 0, cl = 0;
+    return o.preqr == 1 && m > n && qr_shape((int)m, &nb, &cl);
+}
+
+extern "C" size_t psvd_polar_workspace_bytes(int64_t batch, int64_t m, int64_t n, const psvd_opts *opts) {
+    psvd_opts o = resolve_opts(opts);
+    if (batch <= 0 || m <= 0 || n <= 0) return 0;
+    if (polar_use_preqr(o, m, n)) {
+        PolarPreqr l;
+        l.plan(nullptr, 0, batch, m, n, o);
+        return l.need + 256;
+    }
+    return polar_direct_bytes(batch, m, n, o);
 }
 
 extern "C" int psvd_polar_fwd(const float *A, float *W, float *H, int64_t batch, int64_t m, int64_t n,
@@ -616,11 +663,51 @@ extern "C" int psvd_polar_fwd(const float *A, float *W, float *H, int64_t batch,
     if ((long long)m * n > (1LL << 31)) return PSVD_ERR_ARG;
     if (int e = check_device()) return e;
     if (ws_bytes < psvd_polar_workspace_bytes(batch, m, n, &o)) return PSVD_ERR_WORKSPACE;
-    Carver cv(ws, ws_bytes);
-    PolarWS w;
-    w.carve(cv, (int)batch, (int)m, (int)n, polar_kcap(o), o.precision);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int B = (int)batch, M = (int)m, N = (int)n;
+    if (!polar_use_preqr(o, m, n)) {
+        Carver cv(ws, ws_bytes);
+        PolarWS w;
+        w.carve(cv, B, M, N, polar_kcap(o), o.precision);
+        if (cv.overflow) return PSVD_ERR_WORKSPACE;
+        return polar_forward(A, W, H, H != nullptr, w, o, info, st);
+    }
+    PolarPreqr l;
+    l.plan(ws, ws_bytes, batch, m, n, o);
+    {
+        Carver cv(l.rest, l.rest_bytes);
+        QrWS qw;
+        qw.carve(cv, B, M, N);
+        if (cv.overflow) return PSVD_ERR_WORKSPACE;
+        PSVD_TRY_RC(qr_factor(A, l.Q, l.R, nullptr, qw, st));
+    }
+    {
+        Carver cv(l.rest, l.rest_bytes);
+        PolarWS w;
+        w.carve(cv, B, N, N, polar_kcap(o), o.precision);
+        if (cv.overflow) return PSVD_ERR_WORKSPACE;
+        PSVD_TRY_RC(polar_forward(l.R, l.WR, H, H != nullptr, w, o, info, st));
+    }
+    // W = Q W_R: B operand B[k][j] = W_R[j][k] (W_R transposed)
+    Carver cv(l.rest, l.rest_bytes);
+    const long long ld = pad_ld(N);
+    float *qhi = cv.take<float>((size_t)B * M * ld), *qlo = cv.take<float>((size_t)B * M * ld);
+    float *whi = cv.take<float>((size_t)B * N * ld), *wlo = cv.take<float>((size_t)B * N * ld);
+    unsigned *err = cv.take<unsigned>(4);
     if (cv.overflow) return PSVD_ERR_WORKSPACE;
-    return polar_forward(A, W, H, H != nullptr, w, o, info, static_cast<cudaStream_t>(stream));
+    SplitOut a, bt;
+    a.hi = qhi; a.lo = qlo; a.ld = ld; a.bstride = (long long)M * ld;
+    bt.hi = whi; bt.lo = wlo; bt.ld = ld; bt.bstride = (long long)N * ld;
+    PSVD_TRY(prepare_operand(l.Q, N, (long long)M * N, B, M, N, false, 1.f, nullptr, a, st));
+    PSVD_TRY(prepare_operand(l.WR, N, (long long)N * N, B, N, N, true, 1.f, nullptr, bt, st));
+    MatView ah = view_of(qhi, M, N, ld, (long long)M * ld, B), al = view_of(qlo, M, N, ld, (long long)M * ld, B);
+    MatView bh = view_of(whi, N, N, ld, (long long)N * ld, B), bl = view_of(wlo, N, N, ld, (long long)N * ld, B);
+    GemmShape s;
+    memset(&s, 0, sizeof(s));
+    s.M = M; s.N = N; s.K = N; s.prec_uniform = PREC_TF32X3; s.err = err;
+    EpiStore e = epi_store_plain(W, N, (long long)M * N, M, N);
+    PSVD_TRY(launch_gemm(nullptr, nullptr, &ah, &al, &bh, &bl, s, B, e, st));
+    return PSVD_OK;
 }
 
 // ------------------------------------------------------------ allocation-free variant
@@ -646,8 +733,9 @@ extern "C" size_t psvd_polar_noalloc_capacity(void) { return kNoAllocScratchByte
 extern "C" int psvd_polar_fwd_noalloc(const float *A, float *W, float *H, int64_t batch, int64_t m, int64_t n,
                                       const psvd_opts *opts, psvd_info *info, void *stream) {
     psvd_opts o = resolve_opts(opts);
-    // the same argument checks as psvd_polar_fwd
-    if (!A || !W || batch <= 0 || n <= 0 || m < n || batch > 65535 || m > (1 << 28) / 1 || !opts_ok(o))
+    // the same argument checks as psvd_polar_fwd; the QR preprocessing needs a workspace
+    if (!A || !W || batch <= 0 || n <= 0 || m < n || batch > 65535 || m > (1 << 28) / 1 || !opts_ok(o) ||
+        o.preqr != 0)
         return PSVD_ERR_ARG;
     if ((long long)m * n > (1LL << 31)) return PSVD_ERR_ARG;
     if (int e = check_device()) return e;

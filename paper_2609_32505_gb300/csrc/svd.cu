@@ -16,6 +16,7 @@
 
 #include "eigh.cuh"
 #include "polar.cuh"
+#include "qr.cuh"
 
 namespace psvd {
 
@@ -393,8 +394,10 @@ struct SvdWS {
     float *S = nullptr;         // eigenvalues as FP32 [B][n]
     float *colss = nullptr;     // [B][n]
     int *flag = nullptr, *any = nullptr;
-    float *UT = nullptr, *qtau = nullptr, *qbeta = nullptr, *qbuf = nullptr;
+    float *UT = nullptr, *qtau = nullptr, *qbeta = nullptr, *qbuf = nullptr;   // unblocked QR (large m)
     unsigned *qbar = nullptr;
+    QrWS qw;                    // blocked QR (m within the cluster panel)
+    bool blocked_qr = false;
     float *Vhi = nullptr, *Vlo = nullptr;            // V = (V^T)^T split
     float *Khi = nullptr, *Klo = nullptr, *T1 = nullptr, *T1hi = nullptr, *T1lo = nullptr, *Kt = nullptr;
     float *X = nullptr, *Xneg = nullptr, *X2 = nullptr, *F = nullptr, *Ft = nullptr, *VEt = nullptr;
@@ -415,11 +418,17 @@ struct SvdWS {
         colss = cv.template take<float>(B64 * n);
         flag = cv.template take<int>(B64);
         any = cv.template take<int>(4);
-        UT = cv.template take<float>(B64 * n * m);
-        qtau = cv.template take<float>(B64 * n);
-        qbeta = cv.template take<float>(B64 * n);
-        qbuf = cv.template take<float>(B64 * n * m);
-        qbar = cv.template take<unsigned>(4);
+        int qnb = 0, qcl = 0;
+        blocked_qr = qr_shape(m, &qnb, &qcl);
+        if (blocked_qr) {
+            qw.carve(cv, B, m, n);
+        } else {
+            UT = cv.template take<float>(B64 * n * m);
+            qtau = cv.template take<float>(B64 * n);
+            qbeta = cv.template take<float>(B64 * n);
+            qbuf = cv.template take<float>(B64 * n * m);
+            qbar = cv.template take<unsigned>(4);
+        }
         mflag = cv.template take<int>(B64);
         if (mixed) {
             Vhi = cv.template take<float>(B64 * nn);
@@ -536,7 +545,13 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
     count_launch(1);
     // QR fallback (Appendix A.2), decided on the device: the kernels run for the flagged
     // matrices only and return at once when none is flagged, so nothing is read back.
-    {
+    if (w.blocked_qr) {
+        PSVD_TRY_RC(qr_factor(U, U, nullptr, w.flag, w.qw, st));
+        if (info) {
+            info_qr_kernel<<<(B + 127) / 128, 128, 0, st>>>(info, w.flag, B);
+            count_launch(1);
+        }
+    } else {
         QrParams q;
         q.U = U; q.UT = w.UT; q.tau = w.qtau; q.beta = w.qbeta; q.flag = w.flag; q.bar = w.qbar; q.err = p.err;
         q.B = B; q.m = m; q.n = n;
@@ -650,9 +665,8 @@ static int rerun_flagged(const float *A, float *U, float *S, float *VT, int B, i
     return PSVD_OK;
 }
 
-extern "C" size_t psvd_svd_workspace_bytes(int64_t batch, int64_t m, int64_t n, const psvd_opts *opts) {
-    psvd_opts o = svd_resolve(opts);
-    if (batch <= 0 || m <= 0 || n <= 0) return 0;
+// Workspace of the method on M itself (first pass + room for the rerun of flagged matrices).
+static size_t svd_direct_bytes(int64_t batch, int64_t m, int64_t n, const psvd_opts &o) {
     Sizer s;
     SvdWS w;
     w.carve(s, (int)batch, (int)m, (int)n, o);
@@ -667,6 +681,66 @@ extern "C" size_t psvd_svd_workspace_bytes(int64_t batch, int64_t m, int64_t n, 
     return need + 256;
 }
 
+// The method on M itself: first pass, then (mixed precision or learned schedule) the rerun of
+// the flagged matrices, with its one host synchronization.
+static int svd_direct(const float *A, float *U, float *S, float *VT, int B, int m, int n, const psvd_opts &o,
+                      void *ws, size_t ws_bytes, psvd_info *info, cudaStream_t st) {
+    Carver cv(ws, ws_bytes);
+    SvdWS w;
+    w.carve(cv, B, m, n, o);
+    if (cv.overflow) return PSVD_ERR_WORKSPACE;
+    PSVD_TRY_RC(svd_forward(A, U, S, VT, w, o, info, st));
+    if (w.mixed || w.learned) return rerun_flagged(A, U, S, VT, B, m, n, w, o, ws, ws_bytes, info, st);
+    return PSVD_OK;
+}
+
+// QR preprocessing (Section 4.1, rectangular matrices): M = Q R, SVD of R, U = Q U_R.
+// Layout: Q, R, U_R, then one region shared in turn by the QR, the square pipeline on R and
+// the operands of the final product.
+struct PreqrLayout {
+    float *Q = nullptr, *R = nullptr, *UR = nullptr;
+    char *rest = nullptr;
+    size_t rest_bytes = 0, need = 0;
+    void plan(void *ws, size_t ws_bytes, int64_t B, int64_t m, int64_t n, const psvd_opts &sq) {
+        Carver cv(ws, ws_bytes);
+        Q = cv.take<float>(B * m * n);
+        R = cv.take<float>(B * n * n);
+        UR = cv.take<float>(B * n * n);
+        const size_t head = (size_t)round_up((long long)cv.used, 256);
+        Sizer q;
+        QrWS qw;
+        qw.carve(q, (int)B, (int)m, (int)n);
+        const long long ld = pad_ld(n);
+        const size_t ops = (size_t)(2 * B * m * ld + 2 * B * n * ld) * sizeof(float) + 1024;
+        const size_t region = std::max(std::max(q.used + 256, svd_direct_bytes(B, n, n, sq)), ops);
+        need = head + region;
+        rest = ws ? static_cast<char *>(ws) + head : nullptr;
+        rest_bytes = ws_bytes > head ? ws_bytes - head : 0;
+    }
+};
+
+static psvd_opts square_opts(const psvd_opts &o) {
+    psvd_opts p = o;
+    p.preqr = 0;
+    return p;
+}
+
+static bool use_preqr(const psvd_opts &o, int64_t m, int64_t n) {
+    int nb = 0, cl = 0;
+    return o.preqr && m > n && qr_shape((int)m, &nb, &cl);
+}
+
+extern "C" size_t psvd_svd_workspace_bytes(int64_t batch, int64_t m, int64_t n, const psvd_opts *opts) {
+    psvd_opts o = svd_resolve(opts);
+    if (batch <= 0 || m <= 0 || n <= 0) return 0;
+    if (use_preqr(o, m, n)) {
+        PreqrLayout l;
+        l.plan(nullptr, 0, batch, m, n, square_opts(o));
+        return l.need + 256;
+    }
+    return svd_direct_bytes(batch, m, n, o);
+}
+
 extern "C" int psvd_svd_fwd(const float *A, float *U, float *S, float *VT, int64_t batch, int64_t m, int64_t n,
                             const psvd_opts *opts, void *ws, size_t ws_bytes, psvd_info *info, void *stream) {
     psvd_opts o = svd_resolve(opts);
@@ -677,17 +751,37 @@ extern "C" int psvd_svd_fwd(const float *A, float *U, float *S, float *VT, int64
         return PSVD_ERR_ARG;
     if (o.schedule < PSVD_SCHED_CANS || o.schedule > PSVD_SCHED_PE) return PSVD_ERR_ARG;
     if ((o.schedule == PSVD_SCHED_LEARNED || o.schedule == PSVD_SCHED_PE) && !o.lower_bound) return PSVD_ERR_ARG;
+    if (o.preqr != 0 && o.preqr != 1) return PSVD_ERR_ARG;
     if (int e = check_device()) return e;
     if (ws_bytes < psvd_svd_workspace_bytes(batch, m, n, &o)) return PSVD_ERR_WORKSPACE;
-    Carver cv(ws, ws_bytes);
-    SvdWS w;
-    w.carve(cv, (int)batch, (int)m, (int)n, o);
-    if (cv.overflow) return PSVD_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    PSVD_TRY_RC(svd_forward(A, U, S, VT, w, o, info, st));
-    // mixed precision or the learned schedule: the one host synchronization of this call
-    // (reads which matrices need the rerun on the plain path)
-    if (w.mixed || w.learned)
-        return rerun_flagged(A, U, S, VT, (int)batch, (int)m, (int)n, w, o, ws, ws_bytes, info, st);
-    return PSVD_OK;
+    const int B = (int)batch, M = (int)m, N = (int)n;
+    if (!use_preqr(o, m, n)) return svd_direct(A, U, S, VT, B, M, N, o, ws, ws_bytes, info, st);
+    const psvd_opts sq = square_opts(o);
+    PreqrLayout l;
+    l.plan(ws, ws_bytes, batch, m, n, sq);
+    {
+        Carver cv(l.rest, l.rest_bytes);
+        QrWS qw;
+        qw.carve(cv, B, M, N);
+        if (cv.overflow) return PSVD_ERR_WORKSPACE;
+        PSVD_TRY_RC(qr_factor(A, l.Q, l.R, nullptr, qw, st));
+    }
+    PSVD_TRY_RC(svd_direct(l.R, l.UR, S, VT, B, N, N, sq, l.rest, l.rest_bytes, info, st));
+    // U = Q U_R: B operand B[k][j] = U_R[j][k] (U_R transposed)
+    Carver cv(l.rest, l.rest_bytes);
+    const long long ld = pad_ld(N);
+    float *qhi = cv.take<float>((size_t)B * M * ld), *qlo = cv.take<float>((size_t)B * M * ld);
+    float *uhi = cv.take<float>((size_t)B * N * ld), *ulo = cv.take<float>((size_t)B * N * ld);
+    if (cv.overflow) return PSVD_ERR_WORKSPACE;
+    SplitOut a, bt;
+    a.hi = qhi; a.lo = qlo; a.ld = ld; a.bstride = (long long)M * ld;
+    bt.hi = uhi; bt.lo = ulo; bt.ld = ld; bt.bstride = (long long)N * ld;
+    PSVD_TRY(prepare_operand(l.Q, N, (long long)M * N, B, M, N, false, 1.f, nullptr, a, st));
+    PSVD_TRY(prepare_operand(l.UR, N, (long long)N * N, B, N, N, true, 1.f, nullptr, bt, st));
+    unsigned *err = reinterpret_cast<unsigned *>(cv.take<unsigned>(4));
+    if (cv.overflow) return PSVD_ERR_WORKSPACE;
+    EpiStore e = epi_store_plain(U, N, (long long)M * N, M, N);
+    return gemm3(qhi, qlo, M, N, ld, (long long)M * ld, uhi, ulo, N, ld, (long long)N * ld, B, PREC_TF32X3, e, err,
+                 st);
 }

@@ -153,3 +153,21 @@ def test_config_headline_square_mixed_modes(precision):
     if i["prec_fallback"] == 0:
         # the kept mixed result: the estimate within a factor 3 of the measured error
         assert rec / 3.0 <= i["recon_est"] <= 3.0 * rec + 1e-7, (rec, i["recon_est"])
+
+
+def test_config_low_rank_4096_qr_fallback():
+    # Appendix A.2 / the low-rank study (Tables 4-5): 4096 x 4096 of rank 64 (s_i = 1 on the
+    # rank, 0 after).  The iteration runs to its cap on the null space, the column norms of
+    # U = W V flag the matrix, and the blocked QR repairs U; the result meets the gates.
+    import paper_2609_32505_gb300 as P
+    n, r = 4096, 64
+    s0 = W.kappa_spectrum(n, 1.0, rank=r)
+    A = W.torch_constructed(1100, n, n, s0, device="cuda")
+    U, S, VT, info = P.svd_fwd(A, P.make_opts(), return_info=True)
+    torch.cuda.synchronize()
+    assert info[0]["qr_fallback"] == 1
+    rec, ou, ov = _props(A, U, S, VT)[0]
+    sig = float((S[0].double().cpu() - torch.from_numpy(s0)).abs().max())
+    weyl = 2.0 ** -24 * float(torch.linalg.matrix_norm(A[0].double()))
+    assert sig <= 1e-5 * s0[0] + weyl
+    assert rec <= 1e-5 and ou <= 1e-4 and ov <= 1e-4, (rec, ou, ov)

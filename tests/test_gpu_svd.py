@@ -214,8 +214,8 @@ def test_learned_schedule_miss_is_recomputed_on_the_plain_path(precision):
     lbs[0] = 0.9                                            # far above sigma_min(X0)
     A = torch.from_numpy(np.stack(mats).astype(np.float32)).cuda()
     lb = torch.tensor(lbs, dtype=torch.float32, device="cuda")
-    U, S, VT, info = P.svd_fwd(A, P.make_opts(precision=precision, schedule=P.SCHED_LEARNED, lower_bound=lb,
-                                              budget=4), return_info=True)
+    U, S, VT, info = P.svd_fwd(A, P.make_opts(precision=precision, schedule=P.SCHED_LEARNED, lower_bound=lb),
+                               return_info=True)
     torch.cuda.synchronize()
     assert info[0]["sched_fallback"] == 1 and info[0]["status"] == 0
     assert info[0]["steps_3xtf32"] > 0 and info[0]["qr_fallback"] == 0
