@@ -53,10 +53,11 @@ def test_ablation_setting_kappa_1e6():
         for cur, k in zip(r["residual_curve"], r["steps"]):
             assert len(cur) == k + 1 and cur[-1] <= 1e-5 and cur[-2] > 1e-5, name
     ns, cans, pe, lrn = (res[k]["steps"] for k in ("newton_schulz", "cans", "polar_express_style", "learned"))
-    # Newton-Schulz needs about log_1.5(1 / sigma_min) steps to lift the smallest values;
-    # the optimal cubics get there in far fewer
-    assert all(a > 1.4 * b for a, b in zip(ns, cans))
+    # Newton-Schulz needs about log_1.5(1 / sigma_min) steps to lift the smallest values; the
+    # conservative CANS schedule gets there in fewer, the cubics from a known bound in far fewer
+    assert all(a > b for a, b in zip(ns, cans))
     assert all(a > 1.4 * b for a, b in zip(ns, lrn))
+    assert all(a > 1.4 * b for a, b in zip(ns, pe))
     # the damped schedule plateaus above tol until its undamped step (the behaviour the
     # ablation describes): its curve sits between 1e-5 and 1e-1 for at least two steps
     for cur in res["polar_express_style"]["residual_curve"]:
