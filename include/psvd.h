@@ -101,7 +101,8 @@ void psvd_default_opts(psvd_opts *o);
 
 /* Per-matrix outcome, written to a DEVICE array of `batch` records. */
 typedef struct psvd_info {
-    int   status;          /* PSVD_OK, PSVD_NOT_CONVERGED or PSVD_ERR_NONFINITE         */
+    int   status;          /* PSVD_OK, PSVD_NOT_CONVERGED, PSVD_ERR_NONFINITE, or (svd_fwd)
+                              PSVD_ERR_TIMEOUT if a bounded device wait expired          */
     int   iters;           /* polynomial steps applied                                  */
     int   qr_fallback;     /* 1 if U was re-orthogonalized by QR (Algorithm 1's QR fallback) */
     int   sched_fallback;  /* 1 if the learned schedule missed tol and the conservative
@@ -262,6 +263,22 @@ int psvd_mlp_train_step(float *params, float *grads, float *m1, float *m2, const
 int psvd_mlp_grad(const float *params, const float *F, const float *target, int64_t nb,
                   float *grads, float *loss, void *stream);
 
+/* Training helpers (all DEVICE arrays; F is nb x 8 row-major).
+ * psvd_mlp_standardize -- stats[0..7] = per-feature mean, stats[8..15] = sample standard
+ *   deviation (floored at 1e-6), and, if Fs is not NULL, Fs = (F - mean) / std (nb x 8).
+ * psvd_mlp_fold -- makes a network trained on standardized features act on raw ones:
+ *   W1 <- W1 / std (per input feature), b1 <- b1 - W1 mean (with the new W1).
+ * psvd_mlp_gather -- minibatch rows Fb[i] = F[idx[i]], tb[i] = target[idx[i]], i < nb.
+ * psvd_mlp_calibrate -- the learned bound's safety margin: Y = the network's predictions on F
+ *   (nb floats, out), q = the `quantile` (in [0, 1]) of the over-prediction Y - target
+ *   (linear interpolation between order statistics), margin[0] = exp(-max(q, 0)). */
+int psvd_mlp_standardize(const float *F, int64_t nb, float *Fs, float *stats, void *stream);
+int psvd_mlp_fold(float *params, const float *stats, void *stream);
+int psvd_mlp_gather(const float *F, const float *target, const int *idx, int64_t nb, float *Fb,
+                    float *tb, void *stream);
+int psvd_mlp_calibrate(const float *params, const float *F, const float *target, int64_t nb,
+                       float quantile, float *Y, float *margin, void *stream);
+
 /* ---- QR (Appendix A.2's fallback; Section 4.1's preprocessing) ------------------
  * psvd_qr -- thin QR A = Q R of a batch of m x n matrices (m >= n), diag(R) >= 0, by blocked
  *   Householder: panels of 64 (or 32) columns factored by one thread-block cluster per
@@ -289,6 +306,14 @@ const char *psvd_status_string(int status);
 const char *psvd_last_error(void);
 /* Number of kernels this library has launched in the calling process (all threads). */
 uint64_t psvd_kernel_launch_count(void);
+
+/* Test hook for failure detection (no counterpart in the paper): every grid barrier of the
+ * cooperative kernels (the tridiagonalization, the unblocked QR) polls at most `polls` times
+ * before it records PSVD_ERR_TIMEOUT and lets its CTA run on, so that every CTA returns; 0
+ * restores the default (2^24 polls).  The product kernel's pipeline waits are not affected.
+ * An expired wait turns the status of every psvd_svd_fwd record into PSVD_ERR_TIMEOUT (the
+ * outputs of that call are then garbage).  Process-wide; takes effect at the next call. */
+int psvd_debug_set_barrier_spin(uint32_t polls);
 
 /* Measurement hooks (no counterpart in the paper; used by the benchmark's roofline).
  * psvd_profile_enable(1) makes every launch of the tcgen05 product kernel and of the

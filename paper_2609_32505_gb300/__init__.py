@@ -93,6 +93,10 @@ def lib():
         "psvd_mlp_grad": (ctypes.c_int, [vp, vp, vp, i64, vp, vp, vp]),
         "psvd_mlp_train_step": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_int, vp, vp]),
         "psvd_profile_read": (ctypes.c_int, [vp]),
+        "psvd_mlp_standardize": (ctypes.c_int, [vp, i64, vp, vp, vp]),
+        "psvd_mlp_fold": (ctypes.c_int, [vp, vp, vp]),
+        "psvd_mlp_gather": (ctypes.c_int, [vp, vp, vp, i64, vp, vp, vp]),
+        "psvd_mlp_calibrate": (ctypes.c_int, [vp, vp, vp, i64, ctypes.c_float, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -390,7 +394,9 @@ def mlp_grad(params: torch.Tensor, feats: torch.Tensor, target: torch.Tensor):
 
 def mlp_train(params: torch.Tensor, feats: torch.Tensor, target: torch.Tensor, steps: int = 500, lr: float = 3e-3,
               batch: int = 1024, seed: int = 0):
-    """Adam on 0.5 mean (y - target)^2 with the library's own kernels; returns the loss curve."""
+    """Adam on 0.5 mean (y - target)^2 with the library's own kernels; returns the loss curve.
+    The minibatch indices are drawn on the host (seeded) and copied once; the rows are
+    gathered on the device (psvd_mlp_gather)."""
     F = feats.contiguous().float()
     tg = target.contiguous().float()
     grads = torch.zeros_like(params)
@@ -400,12 +406,16 @@ def mlp_train(params: torch.Tensor, feats: torch.Tensor, target: torch.Tensor, s
     L = lib()
     g = torch.Generator(device="cpu")
     g.manual_seed(int(seed))
-    curve = []
     nb = F.shape[0]
+    bs = min(batch, nb)
+    idx = torch.randint(0, nb, (steps, bs), generator=g, dtype=torch.int32).to(F.device)
+    Fb = torch.empty(bs, 8, device=F.device)
+    tb = torch.empty(bs, device=F.device)
+    curve = []
     for it in range(1, steps + 1):
-        idx = torch.randint(0, nb, (min(batch, nb),), generator=g).to(F.device)
-        Fb, tb = F[idx].contiguous(), tg[idx].contiguous()
-        _check(L.psvd_mlp_train_step(_ptr(params), _ptr(grads), _ptr(m1), _ptr(m2), _ptr(Fb), _ptr(tb), Fb.shape[0],
+        _check(L.psvd_mlp_gather(_ptr(F), _ptr(tg), _ptr(idx[it - 1]), bs, _ptr(Fb), _ptr(tb), _stream()),
+               "psvd_mlp_gather")
+        _check(L.psvd_mlp_train_step(_ptr(params), _ptr(grads), _ptr(m1), _ptr(m2), _ptr(Fb), _ptr(tb), bs,
                                      float(lr), it, _ptr(loss), _stream()), "psvd_mlp_train_step")
         if it % 50 == 0 or it == 1:
             curve.append(float(loss.item()))
@@ -414,31 +424,32 @@ def mlp_train(params: torch.Tensor, feats: torch.Tensor, target: torch.Tensor, s
 
 def mlp_fit(feats: torch.Tensor, target: torch.Tensor, steps: int = 2000, lr: float = 3e-3, batch: int = 256,
             seed: int = 0):
-    """Trains the MLP with the library's Adam kernels on standardized features, then folds
-    the standardization into the first layer (W1 <- W1 / std, b1 <- b1 - W1 mean / std), so
-    the returned parameters act on raw features.  Returns (params, loss curve)."""
+    """Trains the MLP with the library's Adam kernels on standardized features
+    (psvd_mlp_standardize), then folds the standardization into the first layer
+    (psvd_mlp_fold), so the returned parameters act on raw features.  Returns (params, curve)."""
     F = feats.contiguous().float()
-    mu = F.mean(0)
-    sd = F.std(0).clamp_min(1e-6)
+    L = lib()
+    stats = torch.empty(16, device=F.device)
+    Fs = torch.empty_like(F)
+    _check(L.psvd_mlp_standardize(_ptr(F), F.shape[0], _ptr(Fs), _ptr(stats), _stream()), "psvd_mlp_standardize")
     params = mlp_init(seed=seed, device=F.device)
-    curve = mlp_train(params, ((F - mu) / sd).contiguous(), target, steps=steps, lr=lr, batch=batch, seed=seed)
-    w1 = params[:512].view(64, 8)
-    b1 = params[512:576]
-    w1s = w1 / sd[None, :]
-    params[576 - 64:576] = b1 - (w1s * mu[None, :]).sum(1)
-    params[:512] = w1s.flatten()
+    curve = mlp_train(params, Fs, target, steps=steps, lr=lr, batch=batch, seed=seed)
+    _check(L.psvd_mlp_fold(_ptr(params), _ptr(stats), _stream()), "psvd_mlp_fold")
     return params, curve
 
 
 def mlp_calibrate(params: torch.Tensor, feats: torch.Tensor, target: torch.Tensor, quantile: float = 0.98) -> float:
     """Safety margin for the predicted lower bound: exp(-q) with q the given quantile of the
-    over-prediction y - target on (held-out) training data, so that about that fraction of
-    bounds are true lower bounds; over-predictions are caught by the conservative rerun."""
-    y = mlp_forward(params, feats)
-    over = (y - target.float()).detach().cpu().numpy()
-    import numpy as _np
-    q = float(_np.quantile(over, quantile))
-    return float(_np.exp(-max(q, 0.0)))
+    over-prediction y - target on (held-out) training data (psvd_mlp_calibrate), so that about
+    that fraction of bounds are true lower bounds; over-predictions are caught by the
+    conservative rerun."""
+    F = feats.contiguous().float()
+    tg = target.contiguous().float()
+    y = torch.empty(F.shape[0], device=F.device)
+    margin = torch.empty(1, device=F.device)
+    _check(lib().psvd_mlp_calibrate(_ptr(params), _ptr(F), _ptr(tg), F.shape[0], float(quantile), _ptr(y),
+                                    _ptr(margin), _stream()), "psvd_mlp_calibrate")
+    return float(margin.item())
 
 
 def predict_lower_bound(a: torch.Tensor, params: torch.Tensor, margin: float = 0.5, probes: int = 8,

@@ -173,7 +173,9 @@ constexpr uint32_t kBarrierSpin = 1u << 24;
 // Group barrier over `g` co-resident CTAs (cooperative launch): monotonic counter,
 // bounded spin; on expiry (or an error raised elsewhere) it records the error and
 // lets the CTA run on so that every CTA terminates.
-PSVD_DEV void group_barrier(unsigned *ctr, unsigned target, unsigned *err) {
+// `spin` bounds the polls (kBarrierSpin unless a test lowered it through
+// psvd_debug_set_barrier_spin).
+PSVD_DEV void group_barrier(unsigned *ctr, unsigned target, unsigned *err, uint32_t spin = kBarrierSpin) {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -181,7 +183,7 @@ PSVD_DEV void group_barrier(unsigned *ctr, unsigned target, unsigned *err) {
         for (uint32_t i = 0;; ++i) {
             if (*(volatile unsigned *)ctr >= target) break;
             if (*(volatile unsigned *)err) break;
-            if (i > kBarrierSpin) { atomicOr(err, DEV_ERR_TIMEOUT); break; }
+            if (i > spin) { atomicOr(err, DEV_ERR_TIMEOUT); break; }
             __nanosleep(40);
         }
         __threadfence();
@@ -194,7 +196,7 @@ PSVD_DEV void group_barrier(unsigned *ctr, unsigned target, unsigned *err) {
 // before it by the CTA barrier, become visible with it) and polls the counter with
 // acquire loads until it reaches `target`; bounded, stops early on a raised error word.
 template <int kSleepNs>
-PSVD_DEV void counter_barrier(unsigned *ctr, unsigned target, unsigned *err) {
+PSVD_DEV void counter_barrier(unsigned *ctr, unsigned target, unsigned *err, uint32_t spin = kBarrierSpin) {
     __syncthreads();
     if (threadIdx.x == 0) {
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
@@ -202,7 +204,7 @@ PSVD_DEV void counter_barrier(unsigned *ctr, unsigned target, unsigned *err) {
             unsigned v;
             asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
             if (v >= target) break;
-            if (i > kBarrierSpin) { atomicOr(err, DEV_ERR_TIMEOUT); break; }
+            if (i > spin) { atomicOr(err, DEV_ERR_TIMEOUT); break; }
             if ((i & 63) == 63 && *(volatile unsigned *)err) break;
             if (kSleepNs > 0) __nanosleep(kSleepNs);
         }

@@ -50,6 +50,7 @@ struct TrdParams {
     unsigned *bar, *err;
     int B, n, groups, g, nrp;
     long long ldn;
+    uint32_t spin;           // poll bound of the grid barrier
 };
 
 // Householder step data: x (row k, columns > k, corrected) -> v (v[k+1] = 1), tau, beta.
@@ -191,9 +192,9 @@ __global__ void __launch_bounds__(kTrdThreads, PSVD_TRD_MINB) sytrd_kernel(TrdPa
 #if PSVD_TRD_BARRIER == 1
 #define TRD_BARRIER() flag_barrier_all(arr, cig, P.g, ++nbar, P.err)
 #elif PSVD_TRD_BARRIER == 2
-#define TRD_BARRIER() group_barrier(rel, (unsigned)P.g * (++nbar), P.err)
+#define TRD_BARRIER() group_barrier(rel, (unsigned)P.g * (++nbar), P.err, P.spin)
 #elif PSVD_TRD_BARRIER == 3
-#define TRD_BARRIER() counter_barrier<PSVD_TRD_SLEEP>(rel, (unsigned)P.g * (++nbar), P.err)
+#define TRD_BARRIER() counter_barrier<PSVD_TRD_SLEEP>(rel, (unsigned)P.g * (++nbar), P.err, P.spin)
 #else
 #define TRD_BARRIER() flag_barrier(arr, rel, cig, P.g, ++nbar, P.err)
 #endif
@@ -888,6 +889,7 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
         P.H = Hs; P.Aw = w.Aw; P.Vh = w.Vh; P.tau = w.tau; P.d = w.d; P.e = w.e; P.pbuf = w.pbuf;
         P.bar = w.bar; P.err = w.err; P.B = B; P.n = n; P.groups = w.groups; P.g = trd_ctas_per_group(n); P.nrp = w.nrp;
         P.ldn = ldn;
+        P.spin = barrier_spin();
         const size_t smem = sizeof(float) * 3 * (size_t)ldn;
         PSVD_TRY(cudaFuncSetAttribute(sytrd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int occ = 0;

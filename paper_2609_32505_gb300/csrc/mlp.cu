@@ -352,3 +352,154 @@ extern "C" int psvd_mlp_train_step(float *params, float *grads, float *m1, float
     PSVD_TRY(cudaGetLastError());
     return PSVD_OK;
 }
+
+namespace psvd {
+
+// ------------------------------------------------------------ training helpers
+// Per-feature mean and sample standard deviation over nb rows (one block per feature, FP64
+// sums in a fixed order), floored at 1e-6, and the standardized copy Fs = (F - mean) / std.
+__global__ void feat_stats_kernel(const float *F, int nb, float *stats) {
+    __shared__ double red[32];
+    const int f = blockIdx.x;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += (double)F[(long long)i * kF + f];
+    s = block_sum(s, red);
+    const double mean = s / nb;
+    double q = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const double d = (double)F[(long long)i * kF + f] - mean;
+        q += d * d;
+    }
+    q = block_sum(q, red);
+    if (threadIdx.x == 0) {
+        stats[f] = (float)mean;
+        stats[kF + f] = (float)fmax(sqrt(nb > 1 ? q / (nb - 1) : 0.0), 1e-6);
+    }
+}
+
+__global__ void feat_standardize_kernel(const float *F, const float *stats, long long total, float *Fs) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int f = (int)(t % kF);
+    Fs[t] = (F[t] - stats[f]) / stats[kF + f];
+}
+
+// A network trained on standardized features, made to act on raw ones:
+// W1 <- W1 / std (column-wise), b1 <- b1 - W1_new mean.  One block of kH threads (one per row).
+__global__ void mlp_fold_kernel(float *params, const float *stats) {
+    const int r = threadIdx.x;
+    if (r >= kH) return;
+    float *w = params + kP_W1 + r * kF;
+    float acc = 0.f;
+    for (int f = 0; f < kF; ++f) {
+        w[f] = w[f] / stats[kF + f];
+        acc += w[f] * stats[f];
+    }
+    params[kP_b1 + r] -= acc;
+}
+
+// Minibatch rows: Fb[i] = F[idx[i]], tb[i] = t[idx[i]].
+__global__ void mlp_gather_kernel(const float *F, const float *t, const int *idx, int nbo, float *Fb, float *tb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nbo) return;
+    const int j = idx[i];
+#pragma unroll
+    for (int f = 0; f < kF; ++f) Fb[(long long)i * kF + f] = F[(long long)j * kF + f];
+    tb[i] = t[j];
+}
+
+// margin = exp(-max(q, 0)) with q the `quantile` of the over-prediction d = y - target
+// (linear interpolation between the order statistics d_(k) and d_(k+1), k = floor((nb-1) q),
+// the usual definition).  Each order statistic is found exactly, in one block, by bisection
+// over the 32-bit keys that order the floats (sign bit flipped for positive values, all bits
+// for negative ones): the smallest key K with #{d : key(d) <= K} > k is the key of d_(k).
+PSVD_DEV unsigned order_key(float x) {
+    const unsigned u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+PSVD_DEV float key_value(unsigned k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+__global__ void mlp_margin_kernel(const float *Y, const float *target, int nb, float quantile, float *margin) {
+    __shared__ int cnt[32];
+    const double h = (double)(nb - 1) * quantile;
+    const int k = (int)floor(h);
+    const int nw = (int)(blockDim.x >> 5);
+    float os[2];
+    for (int which = 0; which < 2; ++which) {
+        const int kk = min(k + which, nb - 1);
+        unsigned long long lo = 0, hi = 0xffffffffull;      // answer in [lo, hi]
+        while (lo < hi) {
+            const unsigned long long mid = (lo + hi) >> 1;
+            int c = 0;
+            for (int i = threadIdx.x; i < nb; i += blockDim.x) c += order_key(Y[i] - target[i]) <= (unsigned)mid;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            __syncthreads();
+            if ((threadIdx.x & 31) == 0) cnt[threadIdx.x >> 5] = c;
+            __syncthreads();
+            int tot = 0;
+            for (int w = 0; w < nw; ++w) tot += cnt[w];
+            if (tot > kk) hi = mid; else lo = mid + 1;
+        }
+        os[which] = key_value((unsigned)lo);
+    }
+    if (threadIdx.x == 0) {
+        const double q = (double)os[0] + (h - k) * ((double)os[1] - (double)os[0]);
+        margin[0] = (float)exp(-fmax(q, 0.0));
+    }
+}
+
+}  // namespace psvd
+
+using namespace psvd;
+
+extern "C" int psvd_mlp_standardize(const float *F, int64_t nb, float *Fs, float *stats, void *stream) {
+    if (!F || !stats || nb <= 0 || nb > (1LL << 30)) return PSVD_ERR_ARG;
+    if (int e = check_device()) return e;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    feat_stats_kernel<<<kF, 256, 0, st>>>(F, (int)nb, stats);
+    count_launch(1);
+    if (Fs) {
+        const long long total = nb * kF;
+        feat_standardize_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(F, stats, total, Fs);
+        count_launch(1);
+    }
+    PSVD_TRY(cudaGetLastError());
+    return PSVD_OK;
+}
+
+extern "C" int psvd_mlp_fold(float *params, const float *stats, void *stream) {
+    if (!params || !stats) return PSVD_ERR_ARG;
+    if (int e = check_device()) return e;
+    mlp_fold_kernel<<<1, kH, 0, static_cast<cudaStream_t>(stream)>>>(params, stats);
+    count_launch(1);
+    PSVD_TRY(cudaGetLastError());
+    return PSVD_OK;
+}
+
+extern "C" int psvd_mlp_gather(const float *F, const float *target, const int *idx, int64_t nb, float *Fb,
+                               float *tb, void *stream) {
+    if (!F || !target || !idx || !Fb || !tb || nb <= 0 || nb > (1LL << 30)) return PSVD_ERR_ARG;
+    if (int e = check_device()) return e;
+    mlp_gather_kernel<<<(unsigned)((nb + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(F, target, idx,
+                                                                                                   (int)nb, Fb, tb);
+    count_launch(1);
+    PSVD_TRY(cudaGetLastError());
+    return PSVD_OK;
+}
+
+extern "C" int psvd_mlp_calibrate(const float *params, const float *F, const float *target, int64_t nb,
+                                  float quantile, float *Y, float *margin, void *stream) {
+    if (!params || !F || !target || !Y || !margin || nb <= 0 || nb > (1LL << 30) || !(quantile >= 0.f) ||
+        !(quantile <= 1.f))
+        return PSVD_ERR_ARG;
+    if (int e = check_device()) return e;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    mlp_fwd_kernel<<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(params, F, (int)nb, Y);
+    mlp_margin_kernel<<<1, 1024, 0, st>>>(Y, target, (int)nb, quantile, margin);
+    count_launch(2);
+    PSVD_TRY(cudaGetLastError());
+    return PSVD_OK;
+}

@@ -15,6 +15,11 @@
 namespace psvd {
 
 static char g_err[512] = "";
+static std::atomic<uint32_t> g_barrier_spin{0};
+uint32_t barrier_spin() {
+    const uint32_t v = g_barrier_spin.load(std::memory_order_relaxed);
+    return v ? v : kBarrierSpin;
+}
 static std::atomic<uint64_t> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
@@ -152,6 +157,11 @@ int check_device() {
 extern "C" {
 
 uint64_t psvd_kernel_launch_count(void) { return psvd::g_launches.load(); }
+
+int psvd_debug_set_barrier_spin(uint32_t polls) {
+    psvd::g_barrier_spin.store(polls, std::memory_order_relaxed);
+    return PSVD_OK;
+}
 
 const char *psvd_last_error(void) { return psvd::g_err; }
 

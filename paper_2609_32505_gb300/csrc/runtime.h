@@ -10,6 +10,8 @@
 namespace psvd {
 
 int check_device();
+// Poll bound of the grid barriers of the cooperative kernels (see psvd_debug_set_barrier_spin).
+uint32_t barrier_spin();
 void count_launch(int n);
 
 inline long long round_up(long long x, long long a) { return (x + a - 1) / a * a; }

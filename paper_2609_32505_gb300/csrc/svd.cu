@@ -71,6 +71,7 @@ struct QrParams {
     const int *flag;
     unsigned *bar, *err;
     int B, m, n, g;
+    uint32_t spin;     // poll bound of the grid barrier
 };
 
 __global__ void __launch_bounds__(256) qr_householder_kernel(QrParams P) {
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(256) qr_householder_kernel(QrParams P) {
         const float *U = P.U + (long long)b * m * n;
         for (int c = gw; c < n; c += GW)
             for (int r = lane; r < m; r += 32) UT[(long long)c * m + r] = U[(long long)r * n + c];
-        group_barrier(P.bar, (++nbar) * P.g, P.err);
+        group_barrier(P.bar, (++nbar) * P.g, P.err, P.spin);
         for (int j = 0; j < n; ++j) {
             float *x = UT + (long long)j * m;
             // v_j from column j (rows j..m-1), computed redundantly by every CTA
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(256) qr_householder_kernel(QrParams P) {
                 if (lane == 0) y[j] -= f;
                 for (int r = j + 1 + lane; r < m; r += 32) y[r] -= f * (float)(x[r] * scal);
             }
-            group_barrier(P.bar, (++nbar) * P.g, P.err);
+            group_barrier(P.bar, (++nbar) * P.g, P.err, P.spin);
             if (blockIdx.x == 0) {
                 // store v_j in place (v_j[j] = 1 implicit) once every CTA has used x
                 for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) x[r] = (float)(x[r] * scal);
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(256) qr_householder_kernel(QrParams P) {
                     P.beta[(long long)b * n + j] = (float)beta;
                 }
             }
-            group_barrier(P.bar, (++nbar) * P.g, P.err);
+            group_barrier(P.bar, (++nbar) * P.g, P.err, P.spin);
         }
     }
 }
@@ -382,6 +383,17 @@ __global__ void hilo_store_kernel(const float *hi, const float *lo, int n, long 
     out[(long long)b * n * n + (long long)i * n + j] = hi[o] + lo[o];
 }
 
+// A bounded device-side wait that expired anywhere in the call (product-kernel pipeline,
+// grid barriers of the eigensolver or the QR) turns every record's status into
+// PSVD_ERR_TIMEOUT: the outputs are not to be trusted.
+__global__ void err_status_kernel(const unsigned *e0, const unsigned *e1, const unsigned *e2, psvd_info *info,
+                                  int B) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const unsigned e = (e0 ? *e0 : 0u) | (e1 ? *e1 : 0u) | (e2 ? *e2 : 0u);
+    if (e & DEV_ERR_TIMEOUT) info[b].status = PSVD_ERR_TIMEOUT;
+}
+
 __global__ void info_qr_kernel(psvd_info *info, const int *flag, int B) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < B) info[b].qr_fallback = flag[b];
@@ -554,7 +566,7 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
     } else {
         QrParams q;
         q.U = U; q.UT = w.UT; q.tau = w.qtau; q.beta = w.qbeta; q.flag = w.flag; q.bar = w.qbar; q.err = p.err;
-        q.B = B; q.m = m; q.n = n;
+        q.B = B; q.m = m; q.n = n; q.spin = barrier_spin();
         q.g = std::max(1, std::min(num_sms_svd(), n / 8));
         if (cudaMemsetAsync(w.qbar, 0, sizeof(unsigned) * 4, st)) return PSVD_ERR_CUDA;
         int occ = 0;
@@ -578,6 +590,11 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
         probe_vt_kernel<<<dim3((n + 7) / 8, B), 256, 0, st>>>(VT, Sout, n, w.Yp);
         probe_resid_kernel<<<dim3((m + 7) / 8, B), 256, 0, st>>>(A, U, w.Yp, m, n, w.rsums);
         count_launch(2);
+    }
+    if (info) {
+        err_status_kernel<<<(B + 127) / 128, 128, 0, st>>>(p.err, w.ew.err, w.blocked_qr ? w.qw.err : nullptr, info,
+                                                           B);
+        count_launch(1);
     }
     if (w.mixed || w.learned) {
         rerun_flag_kernel<<<(B + 127) / 128, 128, 0, st>>>(
