@@ -24,8 +24,9 @@
  *    never wait for the GPU, the return value reports argument and launch errors only,
  *    and per-matrix outcomes land in the device-side psvd_info array.  Iterations
  *    whose length is decided on the GPU (the polar steps, the learned schedule's
- *    conservative rerun, the QR fallback) are enqueued for their whole step budget;
- *    launches that find nothing left to do return at once.
+ *    conservative rerun in psvd_polar_fwd) are enqueued for their whole step budget;
+ *    launches that find nothing left to do return at once.  psvd_svd_fwd is the one
+ *    call that synchronizes (see there).
  *  - Calls on the same workspace must not overlap on the GPU.
  */
 #ifndef PSVD_H
@@ -180,9 +181,12 @@ size_t psvd_polar_noalloc_capacity(void);
 /* psvd_svd_fwd -- thin SVD M = U Sigma V^T by Algorithm 1.
  *   U: batch x m x n, S: batch x n (descending, >= 0 up to rounding), VT: batch x n x n
  *   (rows are right singular vectors; each V column's largest-|.| entry is positive).
- *   With PSVD_PREC_FP32 the call is asynchronous.  In the mixed modes it synchronizes
- *   `stream` exactly once, after the mixed pass, to read which matrices failed the
- *   checks above; those are recomputed on the FP32-accurate path in the same call. */
+ *   The call synchronizes `stream` once, after its first pass, to read the per-matrix
+ *   flags: the column-norm check of Algorithm 1 (those matrices get the QR fallback) and,
+ *   in the mixed modes or with the learned schedule, the checks above and the learned
+ *   schedule's misses (those matrices are recomputed on the plain FP32-accurate path, whose
+ *   own QR decision is one more synchronization when it has matrices to recompute).  The
+ *   fallbacks, rare by construction, then run only for the matrices that need them. */
 int psvd_svd_fwd(const float *A, float *U, float *S, float *VT, int64_t batch, int64_t m,
                  int64_t n, const psvd_opts *opts, void *ws, size_t ws_bytes,
                  psvd_info *info, void *stream);

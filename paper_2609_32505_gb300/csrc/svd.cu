@@ -555,34 +555,6 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
     }
     qr_flag_kernel<<<B, 256, 0, st>>>(w.colss, n, o.eps_qr, w.learned ? p.fallback : nullptr, w.flag, w.any);
     count_launch(1);
-    // QR fallback (Appendix A.2), decided on the device: the kernels run for the flagged
-    // matrices only and return at once when none is flagged, so nothing is read back.
-    if (w.blocked_qr) {
-        PSVD_TRY_RC(qr_factor(U, U, nullptr, w.flag, w.qw, st));
-        if (info) {
-            info_qr_kernel<<<(B + 127) / 128, 128, 0, st>>>(info, w.flag, B);
-            count_launch(1);
-        }
-    } else {
-        QrParams q;
-        q.U = U; q.UT = w.UT; q.tau = w.qtau; q.beta = w.qbeta; q.flag = w.flag; q.bar = w.qbar; q.err = p.err;
-        q.B = B; q.m = m; q.n = n; q.spin = barrier_spin();
-        q.g = std::max(1, std::min(num_sms_svd(), n / 8));
-        if (cudaMemsetAsync(w.qbar, 0, sizeof(unsigned) * 4, st)) return PSVD_ERR_CUDA;
-        int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, qr_householder_kernel, 256, 0) != cudaSuccess ||
-            occ * num_sms_svd() < q.g)
-            return PSVD_ERR_CUDA;
-        void *args[] = {&q};
-        if (cudaLaunchCooperativeKernel((void *)qr_householder_kernel, dim3(q.g), dim3(256), args, 0, st) != cudaSuccess)
-            return PSVD_ERR_CUDA;
-        qr_form_q_kernel<<<dim3((n + 7) / 8, B), 256, 0, st>>>(q, w.qbuf);
-        count_launch(2);
-        if (info) {
-            info_qr_kernel<<<(B + 127) / 128, 128, 0, st>>>(info, w.flag, B);
-            count_launch(1);
-        }
-    }
     if (w.mixed) {
         // the mixed result's reconstruction error, estimated from kProbes probes of the final
         // factors, and the decision to keep it or recompute the matrix on the FP32 path
@@ -592,8 +564,7 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
         count_launch(2);
     }
     if (info) {
-        err_status_kernel<<<(B + 127) / 128, 128, 0, st>>>(p.err, w.ew.err, w.blocked_qr ? w.qw.err : nullptr, info,
-                                                           B);
+        err_status_kernel<<<(B + 127) / 128, 128, 0, st>>>(p.err, w.ew.err, nullptr, info, B);
         count_launch(1);
     }
     if (w.mixed || w.learned) {
@@ -603,6 +574,38 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
         count_launch(1);
     }
     return cudaGetLastError() == cudaSuccess ? PSVD_OK : PSVD_ERR_CUDA;
+}
+
+// QR fallback (Appendix A.2) of the matrices with flag[b] != 0 (a device array): U is
+// replaced by the Q of its QR with diag(R) >= 0, in place.
+static int qr_fallback(float *U, SvdWS &w, const int *flag, psvd_info *info, cudaStream_t st) {
+    PolarWS &p = w.pw;
+    const int B = p.B, m = p.m, n = p.n;
+    if (w.blocked_qr) {
+        PSVD_TRY(cudaMemsetAsync(w.qw.err, 0, sizeof(unsigned) * 4, st));
+        PSVD_TRY_RC(qr_factor(U, U, nullptr, flag, w.qw, st));
+    } else {
+        QrParams q;
+        q.U = U; q.UT = w.UT; q.tau = w.qtau; q.beta = w.qbeta; q.flag = flag; q.bar = w.qbar; q.err = p.err;
+        q.B = B; q.m = m; q.n = n; q.spin = barrier_spin();
+        q.g = std::max(1, std::min(num_sms_svd(), n / 8));
+        PSVD_TRY(cudaMemsetAsync(w.qbar, 0, sizeof(unsigned) * 4, st));
+        int occ = 0;
+        PSVD_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, qr_householder_kernel, 256, 0));
+        if (occ * num_sms_svd() < q.g) return cuda_fail(cudaErrorCooperativeLaunchTooLarge, __FILE__, __LINE__);
+        void *args[] = {&q};
+        PSVD_TRY(cudaLaunchCooperativeKernel((void *)qr_householder_kernel, dim3(q.g), dim3(256), args, 0, st));
+        qr_form_q_kernel<<<dim3((n + 7) / 8, B), 256, 0, st>>>(q, w.qbuf);
+        count_launch(2);
+    }
+    if (info) {
+        info_qr_kernel<<<(B + 127) / 128, 128, 0, st>>>(info, flag, B);
+        err_status_kernel<<<(B + 127) / 128, 128, 0, st>>>(w.blocked_qr ? w.qw.err : nullptr, nullptr, nullptr, info,
+                                                           B);
+        count_launch(2);
+    }
+    PSVD_TRY(cudaGetLastError());
+    return PSVD_OK;
 }
 
 }  // namespace psvd
@@ -632,9 +635,9 @@ struct RerunWS {
     float *A = nullptr, *U = nullptr, *S = nullptr, *VT = nullptr;
     psvd_info *info = nullptr;
     int *idx = nullptr, *why = nullptr;   // rerun matrix j is batch entry idx[j], for reasons why[j]
-    SvdWS w;
+    size_t head = 0;                      // bytes of the above; the plain pipeline's region follows
     template <class C>
-    void carve(C &cv, int F, int m, int n, const psvd_opts &plain) {
+    void carve(C &cv, int F, int m, int n) {
         const long long F64 = F;
         A = cv.template take<float>(F64 * m * n);
         U = cv.template take<float>(F64 * m * n);
@@ -643,15 +646,18 @@ struct RerunWS {
         info = cv.template take<psvd_info>(F64);
         idx = cv.template take<int>(F64);
         why = cv.template take<int>(F64);
-        w.carve(cv, F, m, n, plain);
+        head = (size_t)round_up((long long)cv.used, 256);
     }
 };
 
-static int rerun_flagged(const float *A, float *U, float *S, float *VT, int B, int m, int n, const SvdWS &w,
-                         const psvd_opts &o, void *ws, size_t ws_bytes, psvd_info *info, cudaStream_t st) {
-    std::vector<int> flags(B);
-    PSVD_TRY(cudaMemcpyAsync(flags.data(), w.mflag, sizeof(int) * (size_t)B, cudaMemcpyDeviceToHost, st));
-    PSVD_TRY(cudaStreamSynchronize(st));
+static int svd_direct(const float *A, float *U, float *S, float *VT, int B, int m, int n, const psvd_opts &o,
+                      void *ws, size_t ws_bytes, psvd_info *info, cudaStream_t st);
+
+// Recompute the matrices with flags[b] != 0 (host copy of the first pass's reasons) on the
+// plain FP32-accurate path and scatter the results back.
+static int rerun_flagged(const float *A, float *U, float *S, float *VT, int B, int m, int n,
+                         const std::vector<int> &flags, const psvd_opts &o, void *ws, size_t ws_bytes,
+                         psvd_info *info, cudaStream_t st) {
     std::vector<int> idx, why;
     for (int b = 0; b < B; ++b)
         if (flags[b]) { idx.push_back(b); why.push_back(flags[b]); }
@@ -660,14 +666,15 @@ static int rerun_flagged(const float *A, float *U, float *S, float *VT, int B, i
     const psvd_opts po = plain_opts(o);
     Carver cv(ws, ws_bytes);
     RerunWS r;
-    r.carve(cv, F, m, n, po);
-    if (cv.overflow) return PSVD_ERR_WORKSPACE;
+    r.carve(cv, F, m, n);
+    if (cv.overflow || r.head >= ws_bytes) return PSVD_ERR_WORKSPACE;
     const size_t mn = (size_t)m * n, nn = (size_t)n * n;
     PSVD_TRY(cudaMemcpyAsync(r.idx, idx.data(), sizeof(int) * (size_t)F, cudaMemcpyHostToDevice, st));
     PSVD_TRY(cudaMemcpyAsync(r.why, why.data(), sizeof(int) * (size_t)F, cudaMemcpyHostToDevice, st));
     for (int j = 0; j < F; ++j)
         PSVD_TRY(cudaMemcpyAsync(r.A + j * mn, A + idx[j] * mn, sizeof(float) * mn, cudaMemcpyDeviceToDevice, st));
-    PSVD_TRY_RC(svd_forward(r.A, r.U, r.S, r.VT, r.w, po, info ? r.info : nullptr, st));
+    PSVD_TRY_RC(svd_direct(r.A, r.U, r.S, r.VT, F, m, n, po, static_cast<char *>(ws) + r.head, ws_bytes - r.head,
+                           info ? r.info : nullptr, st));
     for (int j = 0; j < F; ++j) {
         const size_t b = (size_t)idx[j];
         PSVD_TRY(cudaMemcpyAsync(U + b * mn, r.U + j * mn, sizeof(float) * mn, cudaMemcpyDeviceToDevice, st));
@@ -689,17 +696,21 @@ static size_t svd_direct_bytes(int64_t batch, int64_t m, int64_t n, const psvd_o
     w.carve(s, (int)batch, (int)m, (int)n, o);
     size_t need = s.used;
     if (o.precision != PSVD_PREC_FP32 || o.schedule == PSVD_SCHED_LEARNED) {
-        // room for rerunning every matrix on the FP32-accurate path
+        // room for rerunning every matrix on the FP32-accurate path: the gathered copies, then
+        // the plain pipeline's own workspace
         Sizer s2;
         RerunWS r;
-        r.carve(s2, (int)batch, (int)m, (int)n, plain_opts(o));
-        need = std::max(need, s2.used);
+        r.carve(s2, (int)batch, (int)m, (int)n);
+        need = std::max(need, r.head + svd_direct_bytes(batch, m, n, plain_opts(o)));
     }
     return need + 256;
 }
 
 // The method on M itself: first pass, then (mixed precision or learned schedule) the rerun of
 // the flagged matrices, with its one host synchronization.
+// The one host synchronization of the call: the first pass's per-matrix flags (QR fallback,
+// and for mixed precision or the learned schedule, the rerun reasons) are read back; the
+// matrices that need it then get the QR fallback, the others the rerun on the plain path.
 static int svd_direct(const float *A, float *U, float *S, float *VT, int B, int m, int n, const psvd_opts &o,
                       void *ws, size_t ws_bytes, psvd_info *info, cudaStream_t st) {
     Carver cv(ws, ws_bytes);
@@ -707,7 +718,23 @@ static int svd_direct(const float *A, float *U, float *S, float *VT, int B, int 
     w.carve(cv, B, m, n, o);
     if (cv.overflow) return PSVD_ERR_WORKSPACE;
     PSVD_TRY_RC(svd_forward(A, U, S, VT, w, o, info, st));
-    if (w.mixed || w.learned) return rerun_flagged(A, U, S, VT, B, m, n, w, o, ws, ws_bytes, info, st);
+    const bool rerun = w.mixed || w.learned;
+    std::vector<int> qflag(B), mflag(B, 0);
+    PSVD_TRY(cudaMemcpyAsync(qflag.data(), w.flag, sizeof(int) * (size_t)B, cudaMemcpyDeviceToHost, st));
+    if (rerun) PSVD_TRY(cudaMemcpyAsync(mflag.data(), w.mflag, sizeof(int) * (size_t)B, cudaMemcpyDeviceToHost, st));
+    PSVD_TRY(cudaStreamSynchronize(st));
+    std::vector<int> qr_only(B, 0);
+    bool any_qr = false, any_rerun = false;
+    for (int b = 0; b < B; ++b) {
+        qr_only[b] = qflag[b] && !mflag[b];     // a rerun matrix gets its own QR decision in the rerun
+        any_qr |= qr_only[b] != 0;
+        any_rerun |= mflag[b] != 0;
+    }
+    if (any_qr) {
+        PSVD_TRY(cudaMemcpyAsync(w.flag, qr_only.data(), sizeof(int) * (size_t)B, cudaMemcpyHostToDevice, st));
+        PSVD_TRY_RC(qr_fallback(U, w, w.flag, info, st));
+    }
+    if (any_rerun) return rerun_flagged(A, U, S, VT, B, m, n, mflag, o, ws, ws_bytes, info, st);
     return PSVD_OK;
 }
 
