@@ -5,6 +5,8 @@
   python -m paper_2609_32505_gb300.microbench eigh  --n 4096
   python -m paper_2609_32505_gb300.microbench svd   --n 4096 --prec 0|1
   python -m paper_2609_32505_gb300.microbench stages --n 4096
+  python -m paper_2609_32505_gb300.microbench qr --m 4096 --n 4096 [--batch B]
+      (psvd_qr, with the time of its product-kernel launches)
   python -m paper_2609_32505_gb300.microbench budget --n 4096 --prec 0|1 [--learned]
       (polar_fwd with the default step budget against one trimmed to the steps the input needs:
        the difference is the time of the launches that found nothing left to do)
@@ -46,7 +48,7 @@ def _time(f, reps: int, warmup: int) -> float:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["gemm", "polar", "eigh", "svd", "stages", "budget"])
+    ap.add_argument("what", choices=["gemm", "polar", "eigh", "svd", "stages", "budget", "qr"])
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--m", type=int, default=0)
     ap.add_argument("--batch", type=int, default=1)
@@ -76,6 +78,23 @@ def main(argv=None):
         _, _, info = P.polar(A, o, want_h=False, return_info=True)
         lb = torch.tensor([0.9 / i["scale"] for i in info], device=dev, dtype=torch.float32)
         o = P.make_opts(precision=a.prec, schedule=P.SCHED_LEARNED, lower_bound=lb)
+    if a.what == "qr":
+        import ctypes
+        L = P.lib()
+        ms = _time(lambda: P.qr(A), a.reps, a.warmup)
+        L.psvd_profile_enable(1)
+        P.qr(A)
+        torch.cuda.synchronize()
+        prof = (ctypes.c_double * 20)()
+        L.psvd_profile_read(prof)
+        L.psvd_profile_enable(0)
+        q, r = P.qr(A)
+        a64 = A.double()
+        rec = max(float(torch.linalg.matrix_norm(a64[b] - q[b].double() @ r[b].double()) /
+                        torch.linalg.matrix_norm(a64[b])) for b in range(A.shape[0]))
+        print(f"qr {a.batch} x {m} x {n}: {ms:.3f} ms; product-kernel launches {int(prof[8])} taking "
+              f"{prof[9]:.3f} ms (with event overhead); recon {rec:.2e}", flush=True)
+        return
     if a.what == "budget":
         _, _, info = P.polar(A, o, want_h=False, return_info=True)
         used = max(i["iters"] for i in info)
