@@ -29,7 +29,7 @@ constexpr size_t kQrSlabMax = 180 * 1024;   // shared memory for one CTA's slab 
 static size_t qr_panel_smem(int m, int nb, int cl) {
     const int S = (m + cl - 1) / cl;
     const size_t slab = std::max<size_t>((size_t)S * nb, (size_t)2 * nb * nb) * sizeof(float);
-    return sizeof(double) * ((size_t)2 * cl * 2 * nb + 4 * nb) + slab;
+    return sizeof(double) * ((size_t)2 * cl * 2 * nb + 5 * nb) + slab;
 }
 
 bool qr_shape(int m, int *nb, int *cl) {
@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(PanelArgs P) {
     double *xch = qsm;                           // [2][CL][2 nb]
     double *part = xch + 2 * CL * 2 * nb;        // [2 nb] this CTA's contribution
     double *tot = part + 2 * nb;                 // [2 nb] cluster totals
-    float *slab = reinterpret_cast<float *>(tot + 2 * nb);
+    // then [nb + 2] floats of per-column coefficients (in the next nb doubles), then the slab
+    float *slab = reinterpret_cast<float *>(tot + 2 * nb + nb);
     const int S = (m - j0 + CL - 1) / CL;
     const int r0 = j0 + rank * S;
     const int nr = max(0, min(m, r0 + S) - r0);
@@ -83,59 +84,74 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(PanelArgs P) {
     for (int k = tid; k < 2 * nb; k += blockDim.x) part[k] = 0.0;
     __syncthreads();
 
+    float *coef = reinterpret_cast<float *>(qsm + 2 * CL * 2 * nb + 4 * nb);   // [nb] f_c' of this column
+    float *scal_s = coef + nb;                                                 // [2] scal, beta
     for (int c = 0; c < pw; ++c) {
         const int j = j0 + c, par = c & 1;
         const int jl = j - r0;
         const bool own = jl >= 0 && jl < nr;
         const int start = max(0, jl + 1);
+        const int live = pw - c;                 // entries c .. pw-1 of the vectors are needed
         const float *x = slab + c * S;
         for (int cc = c + warp; cc < pw; cc += nw) {
             const float *y = slab + cc * S;
             float acc = 0.f;
             for (int rr = start + lane; rr < nr; rr += 32) acc = fmaf(x[rr], y[rr], acc);
-            const double d = warp_sum((double)acc);
+            const ff t = warp_sum(ff{acc, 0.f});     // compensated: the lanes' partials exactly
             if (lane == 0) {
-                part[cc] = d;
+                part[cc] = (double)t.hi + (double)t.lo;
                 part[nb + cc] = own ? (double)y[jl] : 0.0;
             }
         }
         __syncthreads();
-        for (int t = tid; t < CL * 2 * nb; t += blockDim.x) {
-            const int peer = t / (2 * nb), k = t - peer * 2 * nb;
+        for (int t = tid; t < CL * 2 * live; t += blockDim.x) {
+            const int peer = t / (2 * live), k = t - peer * 2 * live;
+            const int e = k < live ? c + k : nb + c + (k - live);
             double *dst = cluster.map_shared_rank(xch + ((long long)par * CL + rank) * 2 * nb, peer);
-            dst[k] = part[k];
+            dst[e] = part[e];
         }
         cluster.sync();
-        for (int k = tid; k < 2 * nb; k += blockDim.x) {
+        for (int k = tid; k < 2 * live; k += blockDim.x) {
+            const int e = k < live ? c + k : nb + c + (k - live);
             double s = 0.0;
-            for (int q = 0; q < CL; ++q) s += xch[((long long)par * CL + q) * 2 * nb + k];
-            tot[k] = s;
+            for (int q = 0; q < CL; ++q) s += xch[((long long)par * CL + q) * 2 * nb + e];
+            tot[e] = s;
         }
         __syncthreads();
-        const double alpha = tot[nb + c], s2 = tot[c];
-        double beta, tau, scal;
-        if (s2 == 0.0) { beta = alpha; tau = 0.0; scal = 0.0; }
-        else {
-            beta = -copysign(sqrt(alpha * alpha + s2), alpha);
-            tau = (beta - alpha) / beta;
-            scal = 1.0 / (alpha - beta);
+        // the reflector (FP64, once per lane of warp 0; the FP64 pipe is narrow) and the
+        // coefficient f_c' = tau (v^T y_c') = tau (y_c',j + scal P_c') of every later column
+        if (warp == 0) {
+            const double alpha = tot[nb + c], s2 = tot[c];
+            double beta, tau, scal;
+            if (s2 == 0.0) { beta = alpha; tau = 0.0; scal = 0.0; }
+            else {
+                beta = -copysign(sqrt(alpha * alpha + s2), alpha);
+                tau = (beta - alpha) / beta;
+                scal = 1.0 / (alpha - beta);
+            }
+            for (int cc = c + 1 + lane; cc < pw; cc += 32) coef[cc] = (float)(tau * (tot[nb + cc] + tot[cc] * scal));
+            if (lane == 0) {
+                scal_s[0] = (float)scal;
+                scal_s[1] = (float)beta;
+                if (rank == 0) {
+                    P.tau[(long long)b * n + j] = (float)tau;
+                    P.beta[(long long)b * n + j] = (float)beta;
+                }
+            }
         }
-        const float fs = (float)scal;
-        // y -= tau (v^T y) v for the later panel columns, v^T y = y_j + scal * P_c'
+        __syncthreads();
+        const float fs = scal_s[0];
+        // y -= f_c' v for the later panel columns, v = [1; x * scal]
         for (int cc = c + 1 + warp; cc < pw; cc += nw) {
             float *y = slab + cc * S;
-            const float f = (float)(tau * (tot[nb + cc] + tot[cc] * scal));
+            const float f = coef[cc];
             for (int rr = start + lane; rr < nr; rr += 32) y[rr] -= f * (x[rr] * fs);
             if (own && lane == 0) y[jl] -= f;
         }
         __syncthreads();
         float *xw = slab + c * S;
         for (int rr = start + tid; rr < nr; rr += blockDim.x) xw[rr] *= fs;
-        if (own && tid == 0) xw[jl] = (float)beta;
-        if (rank == 0 && tid == 0) {
-            P.tau[(long long)b * n + j] = (float)tau;
-            P.beta[(long long)b * n + j] = (float)beta;
-        }
+        if (own && tid == 0) xw[jl] = scal_s[1];
         __syncthreads();
     }
 
