@@ -26,17 +26,22 @@ namespace cg = cooperative_groups;
 constexpr int kQrThreads = 512;
 constexpr size_t kQrSlabMax = 180 * 1024;   // shared memory for one CTA's slab of the panel
 
+// Slab column stride: odd, so that the lanes of a warp (consecutive columns, same row) fall
+// in distinct shared-memory banks.
+__host__ __device__ inline int qr_slab_stride(int S) { return (S & 1) ? S : S + 1; }
+
 static size_t qr_panel_smem(int m, int nb, int cl) {
-    const int S = (m + cl - 1) / cl;
-    const size_t slab = std::max<size_t>((size_t)S * nb, (size_t)2 * nb * nb) * sizeof(float);
-    return sizeof(double) * ((size_t)2 * cl * 2 * nb + 5 * nb) + slab;
+    const int S = qr_slab_stride((m + cl - 1) / cl);
+    const size_t slab = std::max<size_t>((size_t)S * nb, (size_t)2 * nb * (nb + 1)) * sizeof(float);
+    const size_t red = sizeof(float) * (size_t)kQrThreads;
+    return sizeof(double) * ((size_t)2 * cl * 2 * nb + 5 * nb) + red + slab;
 }
 
 bool qr_shape(int m, int *nb, int *cl) {
     const int nbs[2] = {64, 32}, cls[2] = {8, 16};
     for (int a = 0; a < 2; ++a)
         for (int c = 0; c < 2; ++c) {
-            const int S = (m + cls[c] - 1) / cls[c];
+            const int S = qr_slab_stride((m + cls[c] - 1) / cls[c]);
             if ((size_t)S * nbs[a] * sizeof(float) <= kQrSlabMax) { *nb = nbs[a]; *cl = cls[c]; return true; }
         }
     return false;
@@ -65,93 +70,123 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(PanelArgs P) {
     if (P.skip[b]) return;                       // uniform across the cluster
     extern __shared__ __align__(16) double qsm[];
     const int nb = P.nb, pw = P.pw, j0 = P.j0, m = P.m, n = P.n;
-    double *xch = qsm;                           // [2][CL][2 nb]
-    double *part = xch + 2 * CL * 2 * nb;        // [2 nb] this CTA's contribution
-    double *tot = part + 2 * nb;                 // [2 nb] cluster totals
-    // then [nb + 2] floats of per-column coefficients (in the next nb doubles), then the slab
-    float *slab = reinterpret_cast<float *>(tot + 2 * nb + nb);
+    double *xch = qsm;                           // [2][CL][2 nb] slots, double-buffered by column parity
+    double *part = xch + 2 * CL * 2 * nb;        // [2 nb] (unused rows kept for the layout)
+    float *coef = reinterpret_cast<float *>(part + 4 * nb);   // [nb] f_c' of this column, then [2] scal, beta
+    float *scal_s = coef + nb;
+    float *red = reinterpret_cast<float *>(part + 5 * nb);    // [kQrThreads] row-block partial sums
+    float *slab = red + kQrThreads;                           // [pw][Sp] column-major, Sp odd
     const int S = (m - j0 + CL - 1) / CL;
+    const int Sp = qr_slab_stride(S);
     const int r0 = j0 + rank * S;
     const int nr = max(0, min(m, r0 + S) - r0);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+    const int tid = threadIdx.x;
     const long long ubase = (long long)b * n * P.ldm;
+    // thread -> (column cc, row block rb): the lanes of a warp share rb and hold consecutive columns
+    const int nrb = kQrThreads / nb, cc = tid % nb, rb = tid / nb;
+    const int rbs = (nr + nrb - 1) / nrb;
+    const int rlo = rb * rbs, rhi = min(nr, rlo + rbs);
 
     for (int c = 0; c < pw; ++c) {
         const float *hi = P.UThi + ubase + (long long)(j0 + c) * P.ldm + r0;
         const float *lo = P.UTlo + ubase + (long long)(j0 + c) * P.ldm + r0;
-        for (int rr = tid; rr < nr; rr += blockDim.x) slab[c * S + rr] = hi[rr] + lo[rr];
+        for (int rr = tid; rr < nr; rr += blockDim.x) slab[c * Sp + rr] = hi[rr] + lo[rr];
     }
-    for (int k = tid; k < 2 * nb; k += blockDim.x) part[k] = 0.0;
     __syncthreads();
 
-    float *coef = reinterpret_cast<float *>(qsm + 2 * CL * 2 * nb + 4 * nb);   // [nb] f_c' of this column
-    float *scal_s = coef + nb;                                                 // [2] scal, beta
     for (int c = 0; c < pw; ++c) {
         const int j = j0 + c, par = c & 1;
         const int jl = j - r0;
         const bool own = jl >= 0 && jl < nr;
         const int start = max(0, jl + 1);
         const int live = pw - c;                 // entries c .. pw-1 of the vectors are needed
-        const float *x = slab + c * S;
-        for (int cc = c + warp; cc < pw; cc += nw) {
-            const float *y = slab + cc * S;
-            float acc = 0.f;
-            for (int rr = start + lane; rr < nr; rr += 32) acc = fmaf(x[rr], y[rr], acc);
-            const ff t = warp_sum(ff{acc, 0.f});     // compensated: the lanes' partials exactly
-            if (lane == 0) {
-                part[cc] = (double)t.hi + (double)t.lo;
-                part[nb + cc] = own ? (double)y[jl] : 0.0;
+        const float *x = slab + c * Sp;
+        // partial dot products of column c with columns cc >= c over rows r > j of this block
+        if (cc >= c && cc < pw) {
+            const float *y = slab + cc * Sp;
+            float a0 = 0.f, a1 = 0.f;
+            int rr = max(rlo, start);
+            for (; rr + 1 < rhi; rr += 2) {
+                a0 = fmaf(x[rr], y[rr], a0);
+                a1 = fmaf(x[rr + 1], y[rr + 1], a1);
             }
+            if (rr < rhi) a0 = fmaf(x[rr], y[rr], a0);
+            red[rb * nb + cc] = a0 + a1;
+        }
+        // the previous column becomes its reflector (v below the diagonal, beta on it); no
+        // thread reads it in this phase (the dot products above start at column c)
+        if (c > 0) {
+            const int jlp = j - 1 - r0;
+            float *xp = slab + (c - 1) * Sp;
+            const float fsp = scal_s[0];
+            for (int rr = max(0, jlp + 1) + tid; rr < nr; rr += blockDim.x) xp[rr] *= fsp;
+            if (jlp >= 0 && jlp < nr && tid == 0) xp[jlp] = scal_s[1];
         }
         __syncthreads();
+        // this CTA's vector (sum over the row blocks; the row-j values from its owner) into a
+        // slot of every CTA of the cluster
         for (int t = tid; t < CL * 2 * live; t += blockDim.x) {
             const int peer = t / (2 * live), k = t - peer * 2 * live;
-            const int e = k < live ? c + k : nb + c + (k - live);
+            double v;
+            int e;
+            if (k < live) {
+                e = c + k;
+                float s = 0.f;
+                for (int q = 0; q < nrb; ++q) s += red[q * nb + e];
+                v = (double)s;
+            } else {
+                e = nb + c + (k - live);
+                v = own ? (double)slab[(e - nb) * Sp + jl] : 0.0;
+            }
             double *dst = cluster.map_shared_rank(xch + ((long long)par * CL + rank) * 2 * nb, peer);
-            dst[e] = part[e];
+            dst[e] = v;
         }
         cluster.sync();
-        for (int k = tid; k < 2 * live; k += blockDim.x) {
-            const int e = k < live ? c + k : nb + c + (k - live);
-            double s = 0.0;
-            for (int q = 0; q < CL; ++q) s += xch[((long long)par * CL + q) * 2 * nb + e];
-            tot[e] = s;
-        }
-        __syncthreads();
-        // the reflector (FP64, once per lane of warp 0; the FP64 pipe is narrow) and the
-        // coefficient f_c' = tau (v^T y_c') = tau (y_c',j + scal P_c') of every later column
-        if (warp == 0) {
-            const double alpha = tot[nb + c], s2 = tot[c];
-            double beta, tau, scal;
-            if (s2 == 0.0) { beta = alpha; tau = 0.0; scal = 0.0; }
+        // warp 0: the cluster totals, the reflector (FP32, as single-precision Householder QR
+        // computes it) and the coefficient f_c' = tau (v^T y_c') = tau (y_c',j + scal P_c')
+        if (tid < 32) {
+            const int lane = tid;
+            const double *slots = xch + (long long)par * CL * 2 * nb;
+            double alpha = 0.0, s2 = 0.0;
+            for (int q = 0; q < CL; ++q) { alpha += slots[q * 2 * nb + nb + c]; s2 += slots[q * 2 * nb + c]; }
+            const float fa = (float)alpha, f2 = (float)s2;
+            float beta, tau, scal;
+            if (f2 == 0.f) { beta = fa; tau = 0.f; scal = 0.f; }
             else {
-                beta = -copysign(sqrt(alpha * alpha + s2), alpha);
-                tau = (beta - alpha) / beta;
-                scal = 1.0 / (alpha - beta);
+                beta = -copysignf(sqrtf(fmaf(fa, fa, f2)), fa);
+                tau = (beta - fa) / beta;
+                scal = 1.f / (fa - beta);
             }
-            for (int cc = c + 1 + lane; cc < pw; cc += 32) coef[cc] = (float)(tau * (tot[nb + cc] + tot[cc] * scal));
+            for (int k = c + 1 + lane; k < pw; k += 32) {
+                double pc = 0.0, yj = 0.0;
+                for (int q = 0; q < CL; ++q) { pc += slots[q * 2 * nb + k]; yj += slots[q * 2 * nb + nb + k]; }
+                coef[k] = tau * ((float)yj + (float)pc * scal);
+            }
             if (lane == 0) {
-                scal_s[0] = (float)scal;
-                scal_s[1] = (float)beta;
+                scal_s[0] = scal;
+                scal_s[1] = beta;
                 if (rank == 0) {
-                    P.tau[(long long)b * n + j] = (float)tau;
-                    P.beta[(long long)b * n + j] = (float)beta;
+                    P.tau[(long long)b * n + j] = tau;
+                    P.beta[(long long)b * n + j] = beta;
                 }
             }
         }
         __syncthreads();
-        const float fs = scal_s[0];
         // y -= f_c' v for the later panel columns, v = [1; x * scal]
-        for (int cc = c + 1 + warp; cc < pw; cc += nw) {
-            float *y = slab + cc * S;
-            const float f = coef[cc];
-            for (int rr = start + lane; rr < nr; rr += 32) y[rr] -= f * (x[rr] * fs);
-            if (own && lane == 0) y[jl] -= f;
+        if (cc > c && cc < pw) {
+            float *y = slab + cc * Sp;
+            const float f = coef[cc] * scal_s[0];
+            for (int rr = max(rlo, start); rr < rhi; ++rr) y[rr] = fmaf(-f, x[rr], y[rr]);
+            if (own && jl >= rlo && jl < rhi) y[jl] -= coef[cc];
         }
         __syncthreads();
-        float *xw = slab + c * S;
-        for (int rr = start + tid; rr < nr; rr += blockDim.x) xw[rr] *= fs;
-        if (own && tid == 0) xw[jl] = scal_s[1];
+    }
+    if (pw > 0) {                                // the last column's reflector
+        const int jlp = j0 + pw - 1 - r0;
+        float *xp = slab + (pw - 1) * Sp;
+        const float fsp = scal_s[0];
+        for (int rr = max(0, jlp + 1) + tid; rr < nr; rr += blockDim.x) xp[rr] *= fsp;
+        if (jlp >= 0 && jlp < nr && tid == 0) xp[jlp] = scal_s[1];
         __syncthreads();
     }
 
@@ -162,7 +197,7 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(PanelArgs P) {
         const long long o = ubase + (long long)j * P.ldm + r0;
         for (int rr = tid; rr < nr; rr += blockDim.x) {
             const int r = r0 + rr;
-            const float v = slab[c * S + rr];
+            const float v = slab[c * Sp + rr];
             float h, l;
             split_tf32(v, h, l);
             P.UThi[o + rr] = h;
@@ -176,7 +211,7 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(PanelArgs P) {
     for (int t = tid; t < nr * pw; t += blockDim.x) {
         const int rr = t / pw, c = t - rr * pw;
         const int r = r0 + rr, j = j0 + c;
-        const float v = slab[c * S + rr];
+        const float v = slab[c * Sp + rr];
         float h, l;
         split_tf32(r < j ? 0.f : (r == j ? 1.f : v), h, l);
         P.Yhi[ybase + (long long)r * P.ldn + j] = h;
@@ -189,11 +224,10 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(PanelArgs P) {
         if (k < i) continue;
         const int ji = j0 + i, jk = j0 + k;
         float acc = 0.f;
-        for (int rr = 0; rr < nr; ++rr) {
+        for (int rr = max(0, jk - r0); rr < nr; ++rr) {      // Y_r,k = 0 above its diagonal (jk >= ji)
             const int r = r0 + rr;
-            if (r < jk) continue;                  // Y_r,k = 0 above its diagonal (jk >= ji)
-            const float yi = r == ji ? 1.f : slab[i * S + rr];
-            const float yk = r == jk ? 1.f : slab[k * S + rr];
+            const float yi = r == ji ? 1.f : slab[i * Sp + rr];
+            const float yk = r == jk ? 1.f : slab[k * Sp + rr];
             acc = fmaf(yi, yk, acc);
         }
         gp[i * nb + k] = acc;
@@ -201,15 +235,16 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(PanelArgs P) {
     __threadfence();
     cluster.sync();
     if (rank != 0) return;
-    float *G = slab, *T = slab + nb * nb;            // the slab is no longer needed
+    const int ldt = nb + 1;                          // padded rows: conflict-free column access
+    float *G = slab, *T = slab + nb * ldt;           // the slab is no longer needed
     __syncthreads();
     for (int t = tid; t < pw * pw; t += blockDim.x) {
         const int i = t / pw, k = t - i * pw;
         float s = 0.f;
         if (k >= i)
             for (int q = 0; q < CL; ++q) s += P.Gpart[((long long)b * CL + q) * nb * nb + i * nb + k];
-        G[i * nb + k] = s;
-        T[i * nb + k] = 0.f;
+        G[i * ldt + k] = s;
+        T[i * ldt + k] = 0.f;
     }
     __syncthreads();
     // T[c][c] = tau_c, T[:c, c] = -tau_c T[:c, :c] G[:c, c]  (G upper triangle)
@@ -219,14 +254,14 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(PanelArgs P) {
     for (int c = 1; c < pw; ++c) {
         float v = 0.f;
         if (tid < c)
-            for (int l = tid; l < c; ++l) v += T[tid * nb + l] * G[l * nb + c];
+            for (int l = tid; l < c; ++l) v += T[tid * ldt + l] * G[l * ldt + c];
         __syncthreads();
-        if (tid < c) T[tid * nb + c] = -tb[c] * v;
-        if (tid == 0) T[c * nb + c] = tb[c];
+        if (tid < c) T[tid * ldt + c] = -tb[c] * v;
+        if (tid == 0) T[c * ldt + c] = tb[c];
         __syncthreads();
     }
     float *out = P.Tm + ((long long)b * P.npan + P.panel) * nb * nb;
-    for (int t = tid; t < nb * nb; t += blockDim.x) out[t] = T[t];
+    for (int t = tid; t < nb * nb; t += blockDim.x) out[t] = t / nb < pw && t % nb < pw ? T[(t / nb) * ldt + t % nb] : 0.f;
 }
 
 // W2^T[c][i] = sum_l op(T)[i][l] W[l][c], W = sum of the ks K-split slices of Y^T X; op = T^T
