@@ -197,6 +197,20 @@ int psvd_svd_fwd(const float *A, float *U, float *S, float *VT, int64_t batch, i
 int psvd_eigh(const float *Hs, float *S, float *VT, int64_t batch, int64_t n,
               void *ws, size_t ws_bytes, void *stream);
 
+/* psvd_eigh_dc -- the same EVD by spectral divide and conquer on the polar decomposition,
+ *   nearly all of it products on the tensor cores: W = sign(H - mu I) as the polar factor of
+ *   H - mu I by the CANS iteration of Algorithm 1 (mu = the median of diag(H)), the projector
+ *   P = (I + W)/2, orthonormal bases V1, V2 of range(P) and range(I - P) as polar factors of
+ *   P Omega and (I - P) Omega' (Omega a fixed seeded Gaussian) refined once through P, then the
+ *   halves V1^T H V1 and V2^T H V2 recursively, with blocks of at most 512 rows (or below
+ *   depth 6) solved by the tridiagonal eigensolver of psvd_eigh; V = [V1 Z1, V2 Z2].  Same
+ *   outputs and conventions as psvd_eigh.  The matrices of the batch are solved in turn, and
+ *   the call synchronizes `stream` at every split (it reads mu and trace(P)).  Workspace:
+ *   psvd_eigh_dc_workspace_bytes(n), for one matrix at a time. */
+size_t psvd_eigh_dc_workspace_bytes(int64_t n);
+int psvd_eigh_dc(const float *Hs, float *S, float *VT, int64_t batch, int64_t n, void *ws,
+                 size_t ws_bytes, void *stream);
+
 /* ---- backward ----------------------------------------------------------------
  * psvd_svd_bwd -- Algorithm 4's backward pass from the cached factors:
  *   W = U V^T, Wbar = Ubar V^T, Vbar_tot = Vbar + W^T Ubar,

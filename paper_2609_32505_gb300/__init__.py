@@ -83,6 +83,8 @@ def lib():
         "psvd_polar_bwd": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, i64, i64, i64, ctypes.c_double, vp, sz, vp]),
         "psvd_eigh_bwd_workspace_bytes": (sz, [i64, i64]),
         "psvd_eigh_bwd": (ctypes.c_int, [vp, vp, vp, vp, vp, i64, i64, ctypes.c_double, ctypes.c_int, vp, sz, vp]),
+        "psvd_eigh_dc_workspace_bytes": (sz, [i64]),
+        "psvd_eigh_dc": (ctypes.c_int, [vp, vp, vp, i64, i64, vp, sz, vp]),
         "psvd_qr_workspace_bytes": (sz, [i64, i64, i64]),
         "psvd_qr": (ctypes.c_int, [vp, vp, vp, i64, i64, i64, vp, sz, vp]),
         "psvd_profile_enable": (ctypes.c_int, [ctypes.c_int]),
@@ -212,6 +214,19 @@ def eigh(h: torch.Tensor):
     L = lib()
     ws = _workspace(L.psvd_eigh_workspace_bytes(bt, n), Hs.device)
     _check(L.psvd_eigh(_ptr(Hs), _ptr(S), _ptr(VT), bt, n, _ptr(ws), ws.numel(), _stream()), "psvd_eigh")
+    return (S[0], VT[0]) if sq else (S, VT)
+
+
+def eigh_dc(h: torch.Tensor):
+    """Symmetric EVD by spectral divide and conquer on the polar decomposition (psvd_eigh_dc):
+    returns (S descending, V^T) for a batch of n x n."""
+    Hs, sq = _batched(h.contiguous().float())
+    bt, n, _ = Hs.shape
+    S = torch.empty(bt, n, device=Hs.device, dtype=torch.float32)
+    VT = torch.empty(bt, n, n, device=Hs.device, dtype=torch.float32)
+    L = lib()
+    ws = _workspace(L.psvd_eigh_dc_workspace_bytes(n), Hs.device)
+    _check(L.psvd_eigh_dc(_ptr(Hs), _ptr(S), _ptr(VT), bt, n, _ptr(ws), ws.numel(), _stream()), "psvd_eigh_dc")
     return (S[0], VT[0]) if sq else (S, VT)
 
 

@@ -5,6 +5,7 @@
   python -m paper_2609_32505_gb300.microbench eigh  --n 4096
   python -m paper_2609_32505_gb300.microbench svd   --n 4096 --prec 0|1
   python -m paper_2609_32505_gb300.microbench stages --n 4096
+  python -m paper_2609_32505_gb300.microbench eigh_dc --n 4096     (divide and conquer, against eigh)
   python -m paper_2609_32505_gb300.microbench qr --m 4096 --n 4096 [--batch B]
       (psvd_qr, with the time of its product-kernel launches)
   python -m paper_2609_32505_gb300.microbench budget --n 4096 --prec 0|1 [--learned]
@@ -48,7 +49,7 @@ def _time(f, reps: int, warmup: int) -> float:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["gemm", "polar", "eigh", "svd", "stages", "budget", "qr"])
+    ap.add_argument("what", choices=["gemm", "polar", "eigh", "svd", "stages", "budget", "qr", "eigh_dc"])
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--m", type=int, default=0)
     ap.add_argument("--batch", type=int, default=1)
@@ -78,6 +79,18 @@ def main(argv=None):
         _, _, info = P.polar(A, o, want_h=False, return_info=True)
         lb = torch.tensor([0.9 / i["scale"] for i in info], device=dev, dtype=torch.float32)
         o = P.make_opts(precision=a.prec, schedule=P.SCHED_LEARNED, lower_bound=lb)
+    if a.what == "eigh_dc":
+        _, H = P.polar(A, P.make_opts())
+        ms = _time(lambda: P.eigh_dc(H), a.reps, a.warmup)
+        ms_t = _time(lambda: P.eigh(H), a.reps, a.warmup)
+        s1, v1 = P.eigh_dc(H)
+        s2, v2 = P.eigh(H)
+        h = H[0].double()
+        v = v1[0].double().T
+        res = float(torch.linalg.matrix_norm(h @ v - v * s1[0].double()) / torch.linalg.matrix_norm(h))
+        print(f"eigh_dc n={n}: {ms:.3f} ms (tridiagonal eigh {ms_t:.3f} ms); max |s_dc - s_tri| / s_max "
+              f"{float((s1 - s2).abs().max() / s2.abs().max()):.2e}; ||H V - V S|| / ||H|| {res:.2e}", flush=True)
+        return
     if a.what == "qr":
         import ctypes
         L = P.lib()
