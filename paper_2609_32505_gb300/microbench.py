@@ -6,6 +6,9 @@
   python -m paper_2609_32505_gb300.microbench svd   --n 4096 --prec 0|1
   python -m paper_2609_32505_gb300.microbench stages --n 4096
   python -m paper_2609_32505_gb300.microbench eigh_dc --n 4096     (divide and conquer, against eigh)
+  python -m paper_2609_32505_gb300.microbench step --n 4096 [--prec 0]
+      (the benchmark's step: learned bound, svd_fwd, svd_bwd; mixed unless --prec 0 -- the
+       command the profiles' launch lists and kernel captures run)
   python -m paper_2609_32505_gb300.microbench qr --m 4096 --n 4096 [--batch B]
       (psvd_qr, with the time of its product-kernel launches)
   python -m paper_2609_32505_gb300.microbench budget --n 4096 --prec 0|1 [--learned]
@@ -49,7 +52,7 @@ def _time(f, reps: int, warmup: int) -> float:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["gemm", "polar", "eigh", "svd", "stages", "budget", "qr", "eigh_dc"])
+    ap.add_argument("what", choices=["gemm", "polar", "eigh", "svd", "stages", "budget", "qr", "eigh_dc", "step"])
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--m", type=int, default=0)
     ap.add_argument("--batch", type=int, default=1)
@@ -79,6 +82,31 @@ def main(argv=None):
         _, _, info = P.polar(A, o, want_h=False, return_info=True)
         lb = torch.tensor([0.9 / i["scale"] for i in info], device=dev, dtype=torch.float32)
         o = P.make_opts(precision=a.prec, schedule=P.SCHED_LEARNED, lower_bound=lb)
+    if a.what == "step":
+        import ctypes
+        from paper_2609_32505_gb300 import train_schedule
+        L = P.lib()
+        params, margin, nprobe = train_schedule.load(device=dev)
+        Z = P.rademacher_probes(1, n, nprobe, seed=5, device=dev)
+        mixed = a.prec != 0
+        g = torch.Generator(device="cpu")
+        g.manual_seed(2000)
+        GU = torch.randn(1, m, n, generator=g).to(dev)
+        GS = torch.randn(1, n, generator=g).to(dev)
+        GVT = torch.randn(1, n, n, generator=g).to(dev)
+
+        def one():
+            if mixed:
+                lb = P.predict_lower_bound(A, params, margin=margin, z=Z)
+                o = P.make_opts(precision=P.PREC_MIXED, schedule=P.SCHED_LEARNED, lower_bound=lb)
+            else:
+                o = P.make_opts()
+            u, s, vt = P.svd_fwd(A, o)
+            P.svd_bwd(A, u, s, vt, GU, GS, GVT, eps=1e-8, kreg_mode=0)
+        ms = _time(one, a.reps, a.warmup)
+        print(f"step n={n} {'mixed' if mixed else 'plain'}: {ms:.3f} ms, {P.kernel_launches()} launches so far",
+              flush=True)
+        return
     if a.what == "eigh_dc":
         _, H = P.polar(A, P.make_opts())
         ms = _time(lambda: P.eigh_dc(H), a.reps, a.warmup)

@@ -69,7 +69,7 @@ def test_eigh_dc_scalar_matrix_and_batch():
     n = 640
     h = np.stack([2.5 * np.eye(n), _spd(620, n, np.linspace(1.0, 0.01, n))])
     s, vt = _run(h)
-    assert np.abs(s[0] - 2.5).max() <= 1e-6
+    assert np.abs(s[0] - 2.5).max() <= 1e-5 * 2.5
     assert np.linalg.norm(vt[0] @ vt[0].T - np.eye(n)) / np.sqrt(n) <= 1e-5
     _check(h[1], s[1], vt[1])
     # the same eigenvalues as the tridiagonal solver

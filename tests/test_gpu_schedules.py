@@ -44,7 +44,8 @@ def test_ablation_setting_kappa_1e6():
     n, bt = 512, 2
     A = W.torch_constructed(1200, n, n, W.kappa_spectrum(n, 1e6), device="cuda", batch=bt)
     _, _, info = P.polar(A, P.make_opts(), return_info=True)
-    lb = torch.tensor([0.5e-6 / i["scale"] for i in info], dtype=torch.float32, device="cuda")
+    # s_i = 1e6^((n-i)/(n-1)): sigma_min(A) = 1, so 0.5 / scale is a valid bound of sigma_min(X0)
+    lb = torch.tensor([0.5 / i["scale"] for i in info], dtype=torch.float32, device="cuda")
     res = S.compare(A, lb, reps=1)
     for name, r in res.items():
         assert all(s == 0 for s in r["status"]), (name, r["status"])
