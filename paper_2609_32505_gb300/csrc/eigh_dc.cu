@@ -13,8 +13,11 @@
 // H_1 = V_1^T H V_1 and H_2 = V_2^T H V_2 are split again, down to leaves of at most kLeaf
 // rows that the tridiagonal eigensolver takes, and V = [V_1 Z_1, V_2 Z_2].  The eigenvalues
 // of H_1 all exceed those of H_2, so the descending order needs no merge.
-// mu is the median of diag(H) (it lies between the extreme eigenvalues).  The host reads mu
-// and k at every split (a synchronization each).
+// mu is the midpoint of the two middle entries of diag(H) (it lies between the extreme
+// eigenvalues).  A block whose diagonal spread and off-diagonal entries are within 1e-5 of
+// its largest diagonal entry (a near multiple of I, whose H - mu I has no defined sign) goes
+// to the leaf solver whole.  The host reads diag(H), its spread and k at every split (two
+// synchronizations each).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -49,6 +52,24 @@ struct Stack {
 __global__ void dc_diag_kernel(const float *H, int n, float *d) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) d[i] = H[(long long)i * n + i];
+}
+
+// *offmax = max |H_ij| over i != j, as the bits of a non-negative float (which order as
+// unsigned integers); *offmax must hold 0 on entry
+__global__ void dc_offmax_kernel(const float *H, int n, unsigned *offmax) {
+    __shared__ float red[32];
+    float m = 0.f;
+    const long long nn = (long long)n * n;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (long long)gridDim.x * blockDim.x)
+        if (t / n != t % n) m = fmaxf(m, fabsf(H[t]));
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+        m = warp_max(m);
+        if (threadIdx.x == 0) atomicMax(offmax, __float_as_uint(m));
+    }
 }
 
 // X = H - mu I
@@ -212,18 +233,33 @@ static int dc_solve(const float *H, int n, float *lam, float *V, int depth, unsi
     float *G = stk.take<float>(nn), *V12 = stk.take<float>(nn), *T = stk.take<float>(nn);
     float *dg = stk.take<float>(n);
     double *tr = stk.take<double>(1);
+    unsigned *om = stk.take<unsigned>(1);
     stk.note();
     int k = n / 2;
     if (!stk.sizing) {
-        if (!tr) return PSVD_ERR_WORKSPACE;
-        // split point: median of the diagonal
+        if (!tr || !om) return PSVD_ERR_WORKSPACE;
         std::vector<float> d(n);
+        unsigned omb = 0;
+        PSVD_TRY(cudaMemsetAsync(om, 0, sizeof(unsigned), st));
         dc_diag_kernel<<<(n + 255) / 256, 256, 0, st>>>(H, n, dg);
-        count_launch(1);
+        dc_offmax_kernel<<<(unsigned)std::min((long long)4 * num_sms(), (nn + 255) / 256), 256, 0, st>>>(H, n, om);
+        count_launch(2);
         PSVD_TRY(cudaMemcpyAsync(d.data(), dg, sizeof(float) * n, cudaMemcpyDeviceToHost, st));
+        PSVD_TRY(cudaMemcpyAsync(&omb, om, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
         PSVD_TRY(cudaStreamSynchronize(st));
-        std::nth_element(d.begin(), d.begin() + n / 2, d.end());
-        const float mu = d[n / 2];
+        std::sort(d.begin(), d.end());
+        float offmax;
+        memcpy(&offmax, &omb, sizeof(float));
+        // a (near) multiple of I has no usable split: H - mu I is at the level of the
+        // rounding of H and its sign is undefined, so the leaf solver takes it whole
+        const float dscale = std::max(std::fabs(d.front()), std::fabs(d.back()));
+        if (!(std::max(d.back() - d.front(), 2.f * offmax) > 1e-5f * dscale)) {
+            stk.top = mark;
+            return dc_leaf(H, n, lam, V, stk, st);
+        }
+        // split point: the midpoint of the two middle diagonal entries, so that a diagonal
+        // input with distinct entries is never split at one of its eigenvalues
+        const float mu = 0.5f * (d[n / 2 - 1] + d[n / 2]);
         const unsigned blocks = (unsigned)((nn + 255) / 256);
         dc_shift_kernel<<<blocks, 256, 0, st>>>(H, n, mu, X);
         count_launch(1);
