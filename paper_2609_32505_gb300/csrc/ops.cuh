@@ -10,6 +10,11 @@ namespace psvd {
 // so that every TMA row stride is 16-byte aligned.
 inline long long pad_ld(long long cols) { return round_up(cols < 1 ? 1 : cols, 32); }
 
+// The column L1 norms of the normalization (Algorithm 2) are summed in slabs of kL1Rows
+// rows; the buffer of column sums holds batch x l1_slabs(m) x n partial sums.
+constexpr int kL1Rows = 256;
+__host__ __device__ inline int l1_slabs(int m) { return m < 1 ? 1 : (m + kL1Rows - 1) / kL1Rows; }
+
 // Output format of an operand-preparation pass.
 struct SplitOut {
     float *hi = nullptr, *lo = nullptr;   // fp32 split (lo may be null: TF32 rounding only)
@@ -92,10 +97,14 @@ struct EpiSubSplit {
     struct Acc {};
     static constexpr bool kElem = true, kPre = true;
     PSVD_DEV bool staged() const { return true; }
+    // Read through the read-only path: every element is read once, before this thread
+    // writes it, and no other thread touches it, so a stale cached copy can only be of an
+    // element already read; the reads of the next chunk may then be issued ahead of this
+    // chunk's stores.
     PSVD_DEV float pre(int b, int r, int c) const {
         if (r >= rows || c >= cols) return 0.f;
         const long long o = b * bs + (long long)r * ld + c;
-        return hi[o] + lo[o];
+        return __ldg(hi + o) + __ldg(lo + o);
     }
     PSVD_DEV void elem_pre(Acc &, int b, int r, int c, float v, float p) const {
         if (r >= rows || c >= cols) return;

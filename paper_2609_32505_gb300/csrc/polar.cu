@@ -44,20 +44,71 @@ __global__ void row_l1_kernel(const float *__restrict__ A, int m, int n, float *
     }
 }
 
-__global__ void col_l1_kernel(const float *__restrict__ A, int m, int n, float *colsum) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
-    if (c >= n) return;
-    const float *a = A + (long long)b * m * n + c;
-    float s = 0.f;
-    for (int i = 0; i < m; ++i) s += fabsf(a[(long long)i * n]);
-    colsum[(long long)b * n + c] = s;
+// Column sums of |A| in row slabs of kL1Rows rows: colpart[b][s][c] = sum over the rows of
+// slab s of |A[i][c]|.  A block of 32 lanes x 8 row lanes; each lane covers 4 columns (one
+// float4 with kVec: n % 4 == 0 and A 16-byte aligned) and sums every 8th row of the slab with
+// 8 loads in flight, then the 8 row lanes are added in a fixed order, so the result does not
+// depend on scheduling.
+template <bool kVec>
+__global__ void __launch_bounds__(256) col_l1_kernel(const float *__restrict__ A, int m, int n, float *colpart) {
+    __shared__ float4 part[8][32];
+    const int lane = threadIdx.x & 31, rl = threadIdx.x >> 5;
+    const int c0 = blockIdx.x * 128 + 4 * lane;
+    const int b = blockIdx.z, S = l1_slabs(m);
+    const float *a = A + (long long)b * m * n;
+    for (int sl = blockIdx.y; sl < S; sl += gridDim.y) {
+        const long long r0 = (long long)sl * kL1Rows;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c0 < n) {
+            for (int t0 = 0; t0 < kL1Rows / 8; t0 += 8) {
+                float4 x[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const long long i = r0 + rl + 8 * (t0 + t);
+                    x[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (i < m) {
+                        const float *q = a + i * n + c0;
+                        if (kVec) x[t] = *reinterpret_cast<const float4 *>(q);
+                        else {
+                            x[t].x = q[0];
+                            if (c0 + 1 < n) x[t].y = q[1];
+                            if (c0 + 2 < n) x[t].z = q[2];
+                            if (c0 + 3 < n) x[t].w = q[3];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    acc.x += fabsf(x[t].x); acc.y += fabsf(x[t].y); acc.z += fabsf(x[t].z); acc.w += fabsf(x[t].w);
+                }
+            }
+        }
+        __syncthreads();                      // the previous slab's sums have been read
+        part[rl][lane] = acc;
+        __syncthreads();
+        if (rl == 0 && c0 < n) {
+            float4 s4 = part[0][lane];
+#pragma unroll
+            for (int r = 1; r < 8; ++r) {
+                const float4 q = part[r][lane];
+                s4.x += q.x; s4.y += q.y; s4.z += q.z; s4.w += q.w;
+            }
+            float *o = colpart + ((long long)b * S + sl) * n + c0;
+            o[0] = s4.x;
+            if (c0 + 1 < n) o[1] = s4.y;
+            if (c0 + 2 < n) o[2] = s4.z;
+            if (c0 + 3 < n) o[3] = s4.w;
+        }
+    }
 }
 
-// Launches both passes on `st`.
-cudaError_t l1_norms(const float *A, int B, int m, int n, float *rowsum, float *colsum, int *nonfinite,
+// Launches both passes on `st`; colpart holds B x l1_slabs(m) x n floats.
+cudaError_t l1_norms(const float *A, int B, int m, int n, float *rowsum, float *colpart, int *nonfinite,
                      cudaStream_t st) {
     row_l1_kernel<<<dim3((unsigned)(((long long)m * 32 + 255) / 256), B), 256, 0, st>>>(A, m, n, rowsum, nonfinite);
-    col_l1_kernel<<<dim3((n + 127) / 128, B), 128, 0, st>>>(A, m, n, colsum);
+    const dim3 gc((n + 127) / 128, std::min(l1_slabs(m), 65535), B);
+    if (((uintptr_t)A & 15) == 0 && (n & 3) == 0) col_l1_kernel<true><<<gc, 256, 0, st>>>(A, m, n, colpart);
+    else col_l1_kernel<false><<<gc, 256, 0, st>>>(A, m, n, colpart);
     count_launch(2);
     return cudaGetLastError();
 }
@@ -70,7 +121,12 @@ __global__ void norm_finalize_kernel(const float *rowsum, const float *colsum, c
     const int b = blockIdx.x;
     float r = 0.f, c = 0.f;
     for (int i = threadIdx.x; i < m; i += blockDim.x) r = fmaxf(r, rowsum[(long long)b * m + i]);
-    for (int j = threadIdx.x; j < n; j += blockDim.x) c = fmaxf(c, colsum[(long long)b * n + j]);
+    const int S = l1_slabs(m);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        float cs = 0.f;                              // slab partial sums, added in slab order
+        for (int q = 0; q < S; ++q) cs += colsum[((long long)b * S + q) * n + j];
+        c = fmaxf(c, cs);
+    }
     r = warp_max(r);
     c = warp_max(c);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -140,6 +196,17 @@ __global__ void schedule_fill_kernel(int B, int K, CoefTable tab, const float *l
             coef[((long long)k * B + b) * 2 + 1] = (float)c.c3;
             lo = nlo;
             hi = nhi;
+            if (!damping && hi - 1.0 < 1e-9 && 1.0 - lo < 1e-9) {
+                // converged interval: c1 = 3/2 + O(e^2), c3 = -1/2 + O(e^2) round to the same
+                // floats for every later half-width e < 1e-9, so the rest of the table is
+                // the next cubic repeated (the FP64 pipe is narrow: this saves ~40 steps)
+                const Cubic f = cans_cubic(lo, hi);
+                for (int r = k + 1; r < K; ++r) {
+                    coef[((long long)r * B + b) * 2 + 0] = (float)f.c1;
+                    coef[((long long)r * B + b) * 2 + 1] = (float)f.c3;
+                }
+                break;
+            }
         }
         budget[b] = learned ? (budget_opt > 0 ? budget_opt : greedy_steps_to(l, 0.5 * tol, K) + 5) : K;
         return;
@@ -481,7 +548,6 @@ int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &
     const int B = w.B, m = w.m, n = w.n;
     const bool learned = o.schedule == PSVD_SCHED_LEARNED;
     if (cudaMemsetAsync(w.rowsum, 0, sizeof(float) * (size_t)B * m, st) ||
-        cudaMemsetAsync(w.colsum, 0, sizeof(float) * (size_t)B * n, st) ||
         cudaMemsetAsync(w.nonfinite, 0, sizeof(int) * (size_t)B, st) ||
         cudaMemsetAsync(w.res, 0, sizeof(double) * (size_t)(w.kcap + 2) * B, st) ||
         cudaMemsetAsync(w.notdone, 0, sizeof(int) * (size_t)(w.kcap + 2), st) ||

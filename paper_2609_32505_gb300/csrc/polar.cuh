@@ -62,7 +62,7 @@ struct PolarWS {
         Hraw = cv.template take<float>(B64 * n * n);
         Hsym = cv.template take<float>(B64 * n * n);
         rowsum = cv.template take<float>(B64 * m);
-        colsum = cv.template take<float>(B64 * n);
+        colsum = cv.template take<float>(B64 * l1_slabs(m) * n);
         scale = cv.template take<float>(B64);
         done = cv.template take<int>(B64);
         fin = cv.template take<int>(B64);

@@ -173,28 +173,51 @@ __global__ void skewT_kernel(const float *Hraw, int n, float *hi, float *lo, lon
 // product X V^T is taken in split-TF32) and -X_hi (B operand of X^2).
 // Also records max |X_ij| per matrix in xmax (float bits; the values are >= 0, and a NaN
 // compares above every finite value, so it forces the fallback).
-__global__ void corr_x_kernel(const float *Kt, const float *S, int n, float *X, float *Xlo, float *Xneg, long long ld,
-                              unsigned *xmax) {
-    const int b = blockIdx.z;
-    const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
-    float ax = 0.f;
-    if (i < n && j < n) {
-        const float si = S[(long long)b * n + i], sj = S[(long long)b * n + j];
-        const float den = si + sj;
-        float k = Kt[(long long)b * n * n + (long long)i * n + j];
-        k = 0.5f * (k - Kt[(long long)b * n * n + (long long)j * n + i]);   // exact skew part
-        const float x = den > 0.f ? k / den : 0.f;
-        float xh, xl;
-        split_tf32(x, xh, xl);
-        X[(long long)b * n * ld + (long long)i * ld + j] = xh;
-        Xlo[(long long)b * n * ld + (long long)i * ld + j] = xl;
-        Xneg[(long long)b * n * ld + (long long)i * ld + j] = -xh;
-        ax = fabsf(x);
+// One block per 32 x 32 tile (32 x 8 threads): the tile of Ktilde and its mirror tile are
+// staged in shared memory, so both reads are coalesced; the tile's largest |X| is reduced in
+// the block and recorded with one atomic.
+__global__ void __launch_bounds__(256) corr_x_kernel(const float *Kt, const float *S, int n, float *X, float *Xlo,
+                                                     float *Xneg, long long ld, unsigned *xmax) {
+    __shared__ float tk[32][33], tm[32][33];
+    __shared__ unsigned wmax[8];
+    const int b = blockIdx.z, i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const float *K = Kt + (long long)b * n * n;
+#pragma unroll
+    for (int r = ty; r < 32; r += 8) {
+        tk[r][tx] = (i0 + r < n && j0 + tx < n) ? K[(long long)(i0 + r) * n + j0 + tx] : 0.f;
+        tm[r][tx] = (j0 + r < n && i0 + tx < n) ? K[(long long)(j0 + r) * n + i0 + tx] : 0.f;
     }
-    unsigned bits = __float_as_uint(ax);
+    __syncthreads();
+    unsigned bits = 0;
+    const int j = j0 + tx;
+#pragma unroll
+    for (int r = ty; r < 32; r += 8) {
+        const int i = i0 + r;
+        if (i < n && j < n) {
+            const float si = S[(long long)b * n + i], sj = S[(long long)b * n + j];
+            const float den = si + sj;
+            const float k = 0.5f * (tk[r][tx] - tm[tx][r]);        // exact skew part
+            const float x = den > 0.f ? k / den : 0.f;
+            float xh, xl;
+            split_tf32(x, xh, xl);
+            const long long o = (long long)b * n * ld + (long long)i * ld + j;
+            X[o] = xh;
+            Xlo[o] = xl;
+            Xneg[o] = -xh;
+            bits = max(bits, __float_as_uint(fabsf(x)));
+        }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, o));
-    if (((threadIdx.y * 16 + threadIdx.x) & 31) == 0 && bits) atomicMax(&xmax[b], bits);
+    if (tx == 0) wmax[ty] = bits;
+    __syncthreads();
+    if (ty == 0 && tx == 0) {
+        unsigned m = wmax[0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) m = max(m, wmax[w]);
+        if (m) atomicMax(&xmax[b], m);
+    }
 }
 
 // ------------------------------------------------------------ reconstruction check
@@ -515,7 +538,8 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
         EpiStore e2 = epi_store_plain(w.Kt, n, (long long)n * n, n, n);
         if (int rc = gemm3(w.T1hi, w.T1lo, n, n, ld, nn, vthi, vtlo, n, ld, nn, B, PREC_TF32X3, e2, p.err, st)) return rc;
         if (cudaMemsetAsync(w.xmax, 0, sizeof(unsigned) * (size_t)B, st)) return PSVD_ERR_CUDA;
-        corr_x_kernel<<<g16, b16, 0, st>>>(w.Kt, w.S, n, w.X, w.Ft, w.Xneg, ld, w.xmax);   // X_lo in Ft
+        corr_x_kernel<<<dim3((n + 31) / 32, (n + 31) / 32, B), dim3(32, 8), 0, st>>>(w.Kt, w.S, n, w.X, w.Ft, w.Xneg,
+                                                                                    ld, w.xmax);   // X_lo in Ft
         sigma_refresh_kernel<<<dim3((n + 7) / 8, B), 256, 0, st>>>(w.X, w.S, n, ld, Sout, nullptr);
         count_launch(2);
         // X^2 = X X   (B operand B[j][k] = X[k][j] = -X[j][k])

@@ -157,9 +157,17 @@ def main(argv=None):
         print(f"polar n={n} prec={a.prec}: {ms:.3f} ms steps bf16/tf32/3xtf32 = "
               f"{i['steps_bf16']}/{i['steps_tf32']}/{i['steps_3xtf32']} ortho {i['ortho_resid']:.2e}", flush=True)
     if a.what in ("eigh", "stages"):
+        import ctypes
         _, H = P.polar(A, P.make_opts())
         ms = _time(lambda: P.eigh(H), a.reps, a.warmup)
-        print(f"eigh n={n}: {ms:.3f} ms", flush=True)
+        L = P.lib()
+        L.psvd_profile_enable(1)
+        P.eigh(H)
+        torch.cuda.synchronize()
+        prof = (ctypes.c_double * 20)()
+        L.psvd_profile_read(prof)
+        L.psvd_profile_enable(0)
+        print(f"eigh n={n}: {ms:.3f} ms (tridiagonalization {prof[4 * 4 + 1]:.3f} ms of one call)", flush=True)
     if a.what in ("svd", "stages"):
         ms = _time(lambda: P.svd_fwd(A, o), a.reps, a.warmup)
         print(f"svd_fwd n={n} prec={a.prec}: {ms:.3f} ms", flush=True)
