@@ -199,14 +199,16 @@ int psvd_eigh(const float *Hs, float *S, float *VT, int64_t batch, int64_t n,
 
 /* psvd_eigh_dc -- the same EVD by spectral divide and conquer on the polar decomposition,
  *   nearly all of it products on the tensor cores: W = sign(H - mu I) as the polar factor of
- *   H - mu I by the CANS iteration of Algorithm 1 (mu = the median of diag(H)), the projector
- *   P = (I + W)/2, orthonormal bases V1, V2 of range(P) and range(I - P) as polar factors of
- *   P Omega and (I - P) Omega' (Omega a fixed seeded Gaussian) refined once through P, then the
- *   halves V1^T H V1 and V2^T H V2 recursively, with blocks of at most 512 rows (or below
- *   depth 6) solved by the tridiagonal eigensolver of psvd_eigh; V = [V1 Z1, V2 Z2].  Same
+ *   H - mu I by the CANS iteration of Algorithm 1 (mu = the midpoint of the two middle
+ *   entries of diag(H)), the projector P = (I + W)/2, orthonormal bases V1, V2 of range(P)
+ *   and range(I - P) as polar factors of P Omega and (I - P) Omega' (Omega a fixed seeded
+ *   Gaussian) refined once through P, then the halves V1^T H V1 and V2^T H V2 recursively,
+ *   with blocks of at most 512 rows (or below depth 6), and blocks within 1e-5 of a multiple
+ *   of I, solved by the tridiagonal eigensolver of psvd_eigh; V = [V1 Z1, V2 Z2].  Same
  *   outputs and conventions as psvd_eigh.  The matrices of the batch are solved in turn, and
- *   the call synchronizes `stream` at every split (it reads mu and trace(P)).  Workspace:
- *   psvd_eigh_dc_workspace_bytes(n), for one matrix at a time. */
+ *   the call synchronizes `stream` twice at every split (it reads diag(H) with the largest
+ *   off-diagonal magnitude, then trace(P)).  Workspace: psvd_eigh_dc_workspace_bytes(n), for
+ *   one matrix at a time. */
 size_t psvd_eigh_dc_workspace_bytes(int64_t n);
 int psvd_eigh_dc(const float *Hs, float *S, float *VT, int64_t batch, int64_t n, void *ws,
                  size_t ws_bytes, void *stream);

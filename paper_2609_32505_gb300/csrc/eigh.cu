@@ -42,6 +42,7 @@ namespace psvd {
 #define PSVD_TRD_SLEEP 40
 #endif
 constexpr int kTrdThreads = PSVD_TRD_THREADS;
+constexpr double kFFEps = 3.5527136788005009e-15;   // 2^-48, the float-float unit roundoff
 struct TrdParams {
     const float *H;
     float *Aw, *Vh, *tau;
@@ -100,13 +101,6 @@ PSVD_DEV void load2_vec4(float *d1, const float *s1, float *d2, const float *s2,
         __syncthreads();
         for (int j = n + threadIdx.x; j < 4 * c1; j += blockDim.x) { d1[j] = 0.f; d2[j] = 0.f; }
     }
-}
-
-// In place: x[j] -= vk w[j] + wk v[j] for j in [jstart, n) (row k+1 corrected by the
-// pending rank-2 update of step k).  Entries below jstart are left as they are and
-// never read afterwards.
-PSVD_DEV void correct_row(float *x, const float *v, const float *w, float vk, float wk, int jstart, int n) {
-    for (int j = jstart + threadIdx.x; j < n; j += blockDim.x) x[j] -= vk * w[j] + wk * v[j];
 }
 
 // One pass over an owned row i: optional rank-2 update with (u_v, u_w) on columns
@@ -177,6 +171,7 @@ PSVD_DEV float row_pass(float *Ai, int jstart, int n, const float *uv, const flo
 __global__ void __launch_bounds__(kTrdThreads, PSVD_TRD_MINB) sytrd_kernel(TrdParams P) {
     extern __shared__ __align__(16) float sm[];
     __shared__ float red[64];
+    __shared__ float s_alpha;
     const int n = P.n;
     const int ln = (int)P.ldn;
     float *bufs[3] = {sm, sm + ln, sm + 2 * ln};
@@ -240,16 +235,37 @@ __global__ void __launch_bounds__(kTrdThreads, PSVD_TRD_MINB) sytrd_kernel(TrdPa
             ff pvp = ff_zero();
             for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) pvp = ff_fma(pvp, bw[j], bv[j]);
             const float K = 0.5f * tau_k * block_sum_ff(pvp, red);
-            for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) bw[j] -= K * bv[j];
-            __syncthreads();
+            const float vk = bv[k + 1];
+            const float wk = __fmaf_rn(-K, vk, bw[k + 1]);     // w_k[k+1], as the loops below form it
             float tau_n = 0.f;
             if (more) {
-                // row k+1 corrected by (v_k, w_k) -> reflector k+1
-                const float vk = bv[k + 1], wk = bw[k + 1];
-                correct_row(bn, bv, bw, vk, wk, k + 2, n);
+                // one pass: w_k = p_k - K v_k; row k+1 corrected by (v_k, w_k) (its entry k+2 is
+                // alpha, the rest enter the norm of reflector k+1), then the norm's reduction,
+                // whose barriers also publish w_k, the corrected row and alpha
+                ff s2p = ff_zero();
+                for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
+                    const float wj = __fmaf_rn(-K, bv[j], bw[j]);
+                    bw[j] = wj;
+                    if (j >= k + 2) {
+                        const float xj = bn[j] - (vk * wj + wk * bv[j]);
+                        bn[j] = xj;
+                        if (j == k + 2) s_alpha = xj;
+                        else s2p = ff_fma(s2p, xj, xj);
+                    }
+                }
+                const float s2 = block_sum_ff(s2p, red);
+                const float alpha = s_alpha;
+                float beta_f, scal;
+                if (s2 == 0.f) { beta_f = alpha; tau_n = 0.f; scal = 0.f; }
+                else {
+                    beta_f = -copysignf(sqrtf(__fmaf_rn(alpha, alpha, s2)), alpha);
+                    tau_n = (beta_f - alpha) / beta_f;
+                    scal = 1.f / (alpha - beta_f);
+                }
+                for (int j = k + 3 + threadIdx.x; j < n; j += blockDim.x) bn[j] *= scal;
+                if (threadIdx.x == 0) bn[k + 2] = 1.f;
                 __syncthreads();
-                double beta;
-                householder_from_row(bn, k + 1, n, red, tau_n, beta);
+                const double beta = beta_f;
                 if (cig == (k + 1) % P.g) {     // the CTAs take turns storing the reflector
                     if (threadIdx.x == 0) {
                         D[k + 1] = (double)akk - 2.0 * (double)vk * (double)wk;
@@ -259,6 +275,9 @@ __global__ void __launch_bounds__(kTrdThreads, PSVD_TRD_MINB) sytrd_kernel(TrdPa
                     for (int j = threadIdx.x; j < n; j += blockDim.x)
                         Vh[(long long)(k + 1) * P.ldn + j] = j > k + 1 ? bn[j] : 0.f;
                 }
+            } else {
+                for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) bw[j] = __fmaf_rn(-K, bv[j], bw[j]);
+                __syncthreads();
             }
             // fused pass: rank-2 update of step k and matrix-vector product of step k+1
             float *pn = P.pbuf + ((long long)grp * 2 + ((k + 1) & 1)) * ln;
@@ -388,32 +407,76 @@ __global__ void tri_bisect_kernel(const double *D, const double *E, int n, doubl
 }
 
 // ------------------------------------------------------------ refinement (FP64)
-// FP64 Sturm count of T - x I (T unscaled), pivots floored at pivmin.
-PSVD_DEV int sturm_count64(const double *__restrict__ d, const double *__restrict__ e, int n, double x,
-                           double pivmin) {
+// Float-float quotient a / b (a, b two-float values, b.hi != 0): the FP32 quotient of the
+// leading words, then one correction from the exact residual a - r b, so that the result
+// carries ~2^-44 relative accuracy on the FP32 pipe.
+PSVD_DEV ff ff_div(ff a, ff b) {
+    const float r = __fdividef(a.hi, b.hi);
+    const float p = __fmul_rn(r, b.hi);
+    const float pe = __fmaf_rn(r, b.hi, -p);                  // r b.hi = p + pe exactly
+    const float res = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), __fsub_rn(a.lo, __fmul_rn(r, b.lo)));
+    const float r2 = __fdividef(res, b.hi);
+    const float h = __fadd_rn(r, r2);
+    return ff{h, __fsub_rn(r2, __fsub_rn(h, r))};
+}
+
+// Sturm count of T/tn - x I in float-float arithmetic (~2^-44 relative, on the FP32 pipe, which
+// GB300 has 64 times as wide as its FP64 pipe).  dd[t] = {d_t / tn, e_{t-1}^2 / tn^2} as
+// float-float pairs (e_{-1} = 0); pivots floored at pivmin (the scaled entries are <= 1, so
+// e^2 / pivmin stays finite).  The count is that of a matrix perturbed by a few units of 2^-44
+// of its norm.
+PSVD_DEV int sturm_count_ff(const float4 *__restrict__ dd, int n, ff x, float pivmin) {
     int c = 0;
-    double q = d[0] - x;
-    if (fabs(q) < pivmin) q = -pivmin;
-    c += q < 0.0;
+    float4 v = dd[0];
+    ff q = ff_add(ff{v.x, v.y}, ff{-x.hi, -x.lo});
+    if (fabsf(q.hi) < pivmin) q = ff{-pivmin, 0.f};
+    c += q.hi < 0.f;
     for (int t = 1; t < n; ++t) {
-        const double et = e[t - 1];
-        q = (d[t] - x) - (et * et) / q;
-        if (fabs(q) < pivmin) q = -pivmin;
-        c += q < 0.0;
+        v = dd[t];
+        const ff a = ff_add(ff{v.x, v.y}, ff{-x.hi, -x.lo});
+        const ff r = ff_div(ff{v.z, v.w}, q);
+        q = ff_add(a, ff{-r.hi, -r.lo});
+        if (fabsf(q.hi) < pivmin) q = ff{-pivmin, 0.f};
+        c += q.hi < 0.f;
     }
     return c;
 }
 
-// Eigenvalues whose FP32 neighbours are closer than `near` * ||T|| are refined in FP64 by
-// 9-way multisection (8 lanes per eigenvalue) from a bracket around the FP32 value, down
-// to ~4 u_64 ||T||.  With such shifts inverse iteration separates gaps down to ~1e-12 ||T||
-// by itself, so the Gram-Schmidt of close eigenvalues stays for near-exact multiplicities.
-__global__ void tri_refine_kernel(const double *D, const double *E, int n, const double *tnorm, double near,
-                                  double *lam) {
+// dd[b][t] = {split(d_t / tn), split(e_{t-1}^2 / tn^2)} for the float-float Sturm counts.
+__global__ void sturm_prep_kernel(const double *D, const double *E, const double *tnorm, int n, float4 *dd) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (t >= n) return;
+    const double tn = tnorm[b], inv = tn > 0.0 ? 1.0 / tn : 0.0;
+    const double dv = D[(long long)b * n + t] * inv;
+    const double ev = t > 0 ? E[(long long)b * n + t - 1] * inv : 0.0;
+    const double e2 = ev * ev;
+    const float dh = (float)dv, eh = (float)e2;
+    dd[(long long)b * n + t] = make_float4(dh, (float)(dv - (double)dh), eh, (float)(e2 - (double)eh));
+}
+
+// 1/a by the hardware's approximate reciprocal refined with two Newton-Raphson steps
+// (y <- y + y (1 - a y), each doubling the correct bits); |a| is kept >= tiny > 0 by the
+// pivot floor, far from the denormal and overflow ranges.
+PSVD_DEV double recip64(double a) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+    double e = fma(-a, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-a, y, 1.0);
+    return fma(y, e, y);
+}
+
+// Eigenvalues whose FP32 neighbours are closer than `near` * ||T|| are refined by 9-way
+// multisection (8 lanes per eigenvalue) from a bracket around the FP32 value, with
+// float-float Sturm counts, down to 16 * 2^-48 ||T|| (~6e-14 ||T||; the FP64 counts that
+// reached 4 u_64 ||T|| kept the narrow FP64 pipe busy for ~30 ms on graded spectra at n = 4096).
+// With such shifts three inverse-iteration solves separate gaps down to ~1e-11 ||T|| by
+// themselves; closer groups get the Gram-Schmidt of tri_cluster_kernel.
+__global__ void tri_refine_kernel(const float4 *DD, int n, const double *tnorm, double near, double *lam) {
     const int b = blockIdx.y;
     const int grp = threadIdx.x >> 3, l = threadIdx.x & 7;
     const int i = blockIdx.x * (blockDim.x >> 3) + grp;     // descending index
-    const double *d = D + (long long)b * n, *e = E + (long long)b * n;
+    const float4 *dd = DD + (long long)b * n;
     double *lb = lam + (long long)b * n;
     const double tn = tnorm[b];
     bool active = i < n && n > 1 && tn > 0.0;
@@ -427,8 +490,14 @@ __global__ void tri_refine_kernel(const double *D, const double *E, int n, const
     }
     const bool refined = active;
     const int j = n - 1 - i;                                 // ascending index
-    const double pivmin = fmax(tn * 1e-290, 1e-300);
-    const double stop = 4.0 * DBL_EPSILON * tn;
+    const float pivmin = 1e-30f;                             // on T / tn
+    const double inv = tn > 0.0 ? 1.0 / tn : 0.0;
+    const double stop = 16.0 * kFFEps * tn;
+    auto count = [&](double x) {
+        const double xs = x * inv;
+        const float xh = (float)xs;
+        return sturm_count_ff(dd, n, ff{xh, (float)(xs - (double)xh)}, pivmin);
+    };
     double w = 64.0 * FLT_EPSILON * tn;
     double lo = mid - w, hi = mid + w;
     const unsigned gshift = (threadIdx.x & 31) & ~7u;
@@ -437,7 +506,7 @@ __global__ void tri_refine_kernel(const double *D, const double *E, int n, const
         bool need = false;
         if (active) {
             const double x = l == 0 ? lo : hi;
-            const int c = l < 2 ? sturm_count64(d, e, n, x, pivmin) : 0;
+            const int c = l < 2 ? count(x) : 0;
             const bool ok = l == 0 ? c <= j : (l == 1 ? c > j : true);
             const unsigned bad = (__ballot_sync(0xffffffffu, !ok) >> gshift) & 0x3u;
             need = bad != 0;
@@ -452,7 +521,7 @@ __global__ void tri_refine_kernel(const double *D, const double *E, int n, const
         if (!__any_sync(0xffffffffu, go)) break;
         const double width = hi - lo;
         const double x = lo + width * ((double)(l + 1) / 9.0);
-        const bool le = go && sturm_count64(d, e, n, x, pivmin) <= j;
+        const bool le = go && count(x) <= j;
         const unsigned bits = (__ballot_sync(0xffffffffu, le) >> gshift) & 0xFFu;
         if (go) {
             const int k = __popc(bits);
@@ -475,7 +544,7 @@ PSVD_DEV double hash_unit(unsigned a, unsigned b) {
 // Eigenvalues closer than kRefineNear ||T|| (by their FP32 values) are refined in FP64;
 // Gram-Schmidt then runs only inside groups closer than kClusterTol ||T||.
 constexpr double kRefineNear = 1e-5;
-constexpr double kClusterTol = 1e-12;
+constexpr double kClusterTol = 1e-11;
 
 struct InvitParams {
     const double *D, *E, *tn;
@@ -489,9 +558,11 @@ struct InvitParams {
 // Each thread owns one eigenvector and walks its length-n recurrences in order.  The
 // operands of every pass are streamed through a per-warp shared-memory ring with
 // cp.async (kIvR stages of kIvJ rows, up to kIvNA arrays), so a warp keeps about
-// (kIvR - 1) kIvJ rows of loads in flight instead of waiting on each one.
-constexpr int kIvJ = 16, kIvR = 4, kIvNA = 4;
-constexpr int kIvStage = kIvNA * kIvJ * 32;                       // doubles per stage
+// (kIvR - 1) kIvJ rows of loads in flight instead of waiting on each one.  (Measured at
+// n = 4096: 8 or 16 vectors per warp instead of 32 leave the time unchanged; each vector's
+// chain of dependent FP64 operations sets it.)
+constexpr int kIvJ = 16, kIvR = 4, kIvNA = 4, kIvW = 32;
+constexpr int kIvStage = kIvNA * kIvJ * kIvW;                     // doubles per stage
 constexpr size_t kIvSmem = sizeof(double) * kIvR * kIvStage;      // 64 KB per warp
 
 PSVD_DEV void cp_async8(double *sdst, const double *gsrc) {
@@ -514,7 +585,7 @@ PSVD_DEV void iv_stream(double *ring, int nsteps, int na, Addr addr, Body body) 
                 if (k >= nsteps) break;
                 for (int a = 0; a < na; ++a) {
                     const double *g = addr(k, a);
-                    if (g) cp_async8(buf + (a * kIvJ + jj) * 32 + lane, g);
+                    if (g) cp_async8(buf + (a * kIvJ + jj) * kIvW + lane, g);
                 }
             }
         }
@@ -527,28 +598,16 @@ PSVD_DEV void iv_stream(double *ring, int nsteps, int na, Addr addr, Body body) 
         for (int jj = 0; jj < kIvJ; ++jj) {
             const int k = st * kIvJ + jj;
             if (k >= nsteps) break;
-            body(k, buf + jj * 32);
+            body(k, buf + jj * kIvW);
         }
         issue(st + kIvR - 1);
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __threadfence_block();   // this pass's stores before the next pass's async reads
 }
-#define IV_SLOT(p, a) (p)[(a) * kIvJ * 32]
+#define IV_SLOT(p, a) (p)[(a) * kIvJ * kIvW]
 
 PSVD_DEV double iv_start(int i, int j) { return hash_unit((unsigned)i, (unsigned)j) + 0.0625; }
-
-// 1/a by the hardware's approximate reciprocal refined with two Newton-Raphson steps
-// (y <- y + y (1 - a y), each doubling the correct bits); |a| is kept >= tiny > 0 by the
-// pivot floor, far from the denormal and overflow ranges.
-PSVD_DEV double recip64(double a) {
-    double y;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
-    double e = fma(-a, y, 1.0);
-    y = fma(y, e, y);
-    e = fma(-a, y, 1.0);
-    return fma(y, e, y);
-}
 
 // Factor T - mu I = P L U (U with two superdiagonals, reciprocal pivots in u0).
 PSVD_DEV void iv_factor(const InvitParams &P, double *ring, const double *D, const double *E, int n, double mu,
@@ -660,7 +719,7 @@ PSVD_DEV double iv_finish(const InvitParams &P, double *ring, const double *D, c
 // One warp per block: 32 eigenvectors, each by inverse iteration from a fixed
 // pseudo-random start.  The bisection shift is accurate to ~1e-7 ||T||: three solves
 // reduce the other components by (shift error / gap)^3.
-__global__ void __launch_bounds__(32) tri_invit_kernel(InvitParams P) {
+__global__ void __launch_bounds__(kIvW) tri_invit_kernel(InvitParams P) {
     extern __shared__ __align__(16) double ivring[];
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= P.count) return;
@@ -702,10 +761,35 @@ __global__ void tri_cluster_kernel(InvitParams P, const double *bisect_lam, doub
     const double *D = P.D + (long long)b * n, *E = P.E + (long long)b * n;
     const double tol = ctol * P.tn[b];
     const double *bl = bisect_lam + (long long)b * n;
+    // links: bit i set when eigenvalues i - 1 and i are closer than tol; found in parallel,
+    // so that the walk below only visits clusters (most spectra have none)
+    constexpr int kLinkWords = 2048;
+    __shared__ unsigned link[kLinkWords];
+    const bool fits = n <= 32 * kLinkWords;
+    int any = 1;
+    if (fits) {
+        for (int q = threadIdx.x; q < (n + 31) / 32; q += blockDim.x) link[q] = 0u;
+        __syncthreads();
+        int mine = 0;
+        for (int i = 1 + threadIdx.x; i < n; i += blockDim.x)
+            if (bl[i - 1] - bl[i] <= tol) { atomicOr(&link[i >> 5], 1u << (i & 31)); mine = 1; }
+        any = __syncthreads_or(mine);
+    }
     int i0 = 0;
-    while (i0 < n) {
+    while (any && i0 < n) {
+        if (fits) {                  // skip to the first link after i0 (bits are read-only now)
+            int i = i0 + 1;
+            while (i < n) {
+                const unsigned wd = link[i >> 5] >> (i & 31);
+                if (wd) { i += __ffs(wd) - 1; break; }
+                i = (i | 31) + 1;
+            }
+            if (i >= n) break;
+            i0 = i - 1;
+        }
         int i1 = i0 + 1;
-        while (i1 < n && bl[i1 - 1] - bl[i1] <= tol) ++i1;
+        if (fits) { while (i1 < n && ((link[i1 >> 5] >> (i1 & 31)) & 1u)) ++i1; }
+        else { while (i1 < n && bl[i1 - 1] - bl[i1] <= tol) ++i1; }
         if (i1 - i0 >= 2) {
             for (int i = i0; i < i1; ++i) {
                 const int ti = base + i;
@@ -737,9 +821,25 @@ __global__ void tri_cluster_kernel(InvitParams P, const double *bisect_lam, doub
         i0 = i1;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double *l = P.lam + (long long)b * n;
-        for (int i = 1; i < n; ++i) if (l[i] > l[i - 1]) l[i] = l[i - 1];
+    // descending order: l[i] <- min(l[0..i]) (a running minimum), as a block scan: each thread
+    // takes a contiguous segment, the segment minima are scanned in shared memory, then every
+    // thread applies its prefix
+    __shared__ double segmin[1024];
+    double *l = P.lam + (long long)b * n;
+    const int T = blockDim.x, seg = (n + T - 1) / T;
+    const int s0 = min(n, (int)threadIdx.x * seg), s1 = min(n, s0 + seg);
+    double mn = INFINITY;
+    for (int i = s0; i < s1; ++i) mn = fmin(mn, l[i]);
+    segmin[threadIdx.x] = mn;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int t = 1; t < T; ++t) segmin[t] = fmin(segmin[t], segmin[t - 1]);
+    __syncthreads();
+    double run = threadIdx.x > 0 ? segmin[threadIdx.x - 1] : INFINITY;
+    for (int i = s0; i < s1; ++i) {
+        const double v = fmin(run, l[i]);
+        if (v != l[i]) l[i] = v;
+        run = v;
     }
 }
 
@@ -801,25 +901,69 @@ __global__ void larft_kernel(const float *Gm, const float *tau, int n, int nblk,
 }
 
 // S2 = S T^T (n x nb), split into TF32 hi/lo; S is the sum of `ks` K-split slices of
-// B x n x kWY each, added in slice order.  One block of kWY threads per row of S.
-__global__ void s_times_tt_kernel(const float *S, int ks, int B, const float *Tm, int n, int nblk, int blk, int nb,
-                                  float *S2hi, float *S2lo) {
-    __shared__ float srow[kWY];
-    const int i = blockIdx.x, b = blockIdx.y, j = threadIdx.x;
+// B x n x kWY each, added in slice order.  One block of kWY threads per kStRows rows of S:
+// T is staged once per block in shared memory with rows padded to kWY + 1 floats (thread j
+// reads row j, so the lanes of a warp hit distinct banks), and each thread forms output
+// column j of all kStRows rows.
+constexpr int kStRows = 16;
+constexpr size_t kStSmem = sizeof(float) * ((size_t)kWY * (kWY + 1) + (size_t)kStRows * kWY);
+__global__ void __launch_bounds__(kWY) s_times_tt_kernel(const float *S, int ks, int B, const float *Tm, int n,
+                                                         int nblk, int blk, int nb, float *S2hi, float *S2lo) {
+    extern __shared__ float stsm[];
+    float *Ts = stsm, *sr = stsm + kWY * (kWY + 1);
+    const int i0 = blockIdx.x * kStRows, b = blockIdx.y, j = threadIdx.x;
+    const float *Tb = Tm + ((long long)b * nblk + blk) * kWY * kWY;
+    // T (kWY x kWY, 16-byte aligned rows) as float4 loads, eight in flight per thread
+    const float4 *T4 = reinterpret_cast<const float4 *>(Tb);
+    for (int q0 = j; q0 < kWY * kWY / 4; q0 += 8 * kWY) {
+        float4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = q0 + u * kWY < kWY * kWY / 4 ? T4[q0 + u * kWY] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u * kWY;
+            if (q >= kWY * kWY / 4) break;
+            float *d = Ts + (4 * q / kWY) * (kWY + 1) + (4 * q) % kWY;
+            d[0] = v[u].x; d[1] = v[u].y; d[2] = v[u].z; d[3] = v[u].w;
+        }
+    }
+    // the kStRows rows of S, every slice's load issued before the sums
     const long long slice = (long long)B * n * kWY;
-    const long long o = (long long)b * n * kWY + (long long)i * kWY + j;
-    float sv = S[o];
-    for (int c = 1; c < ks; ++c) sv += S[c * slice + o];
-    srow[j] = sv;
+#pragma unroll
+    for (int r = 0; r < kStRows; ++r) {
+        const int i = i0 + r;
+        float sv = 0.f;
+        if (i < n) {
+            const long long o = (long long)b * n * kWY + (long long)i * kWY + j;
+            float x[kBtSplit];
+#pragma unroll
+            for (int c = 0; c < kBtSplit; ++c) x[c] = c < ks ? S[c * slice + o] : 0.f;
+            sv = x[0];
+#pragma unroll
+            for (int c = 1; c < kBtSplit; ++c) if (c < ks) sv += x[c];
+        }
+        sr[r * kWY + j] = sv;
+    }
     __syncthreads();
-    const float *Tb = Tm + ((long long)b * nblk + blk) * kWY * kWY + (long long)j * kWY;
-    float acc = 0.f;
+    float acc[kStRows];
+#pragma unroll
+    for (int r = 0; r < kStRows; ++r) acc[r] = 0.f;
     if (j < nb)
-        for (int l = j; l < nb; ++l) acc += srow[l] * Tb[l];
-    float h, lo;
-    split_tf32(acc, h, lo);
-    S2hi[o] = h;
-    S2lo[o] = lo;
+        for (int l = j; l < nb; ++l) {
+            const float t = Ts[j * (kWY + 1) + l];
+#pragma unroll
+            for (int r = 0; r < kStRows; ++r) acc[r] += sr[r * kWY + l] * t;
+        }
+#pragma unroll
+    for (int r = 0; r < kStRows; ++r) {
+        const int i = i0 + r;
+        if (i >= n) break;
+        const long long o = (long long)b * n * kWY + (long long)i * kWY + j;
+        float h, lo;
+        split_tf32(acc[r], h, lo);
+        S2hi[o] = h;
+        S2lo[o] = lo;
+    }
 }
 
 // sign convention + outputs: each row of V^T flipped so its largest-|.| entry is positive
@@ -917,10 +1061,12 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
         count_launch(1);
     }
     {
+        float4 *dd = reinterpret_cast<float4 *>(w.S2lo);   // B x n float4 (S2 is free until stage 4)
+        sturm_prep_kernel<<<dim3((n + 255) / 256, B), 256, 0, st>>>(w.d, w.e, tn, n, dd);
         dim3 g((n + 31) / 32, B);       // 32 eigenvalues x 8 lanes per block
-        tri_refine_kernel<<<g, 256, 0, st>>>(w.d, w.e, n, tn, kRefineNear, w.lam);
+        tri_refine_kernel<<<g, 256, 0, st>>>(dd, n, tn, kRefineNear, w.lam);
         PSVD_TRY(cudaGetLastError());
-        count_launch(1);
+        count_launch(2);
     }
     // keep the eigenvalues for cluster detection
     double *bis = reinterpret_cast<double *>(w.S);   // B*n doubles (S holds B*n*kWY floats)
@@ -934,7 +1080,7 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
         P.D = w.d; P.E = w.e; P.tn = tn; P.lam = w.lam;
         P.xs = w.xs; P.u0 = w.u0; P.u1 = w.u1; P.u2 = w.u2; P.lm = w.lm; P.piv = w.piv;
         P.n = n; P.first = b0 * n; P.count = nb * n; P.stride = w.chunk;
-        tri_invit_kernel<<<(P.count + 31) / 32, 32, kIvSmem, st>>>(P);
+        tri_invit_kernel<<<(P.count + kIvW - 1) / kIvW, kIvW, kIvSmem, st>>>(P);
         tri_cluster_kernel<<<nb, 256, 0, st>>>(P, bis, kClusterTol);
         dim3 g((n + 31) / 32, (n + 31) / 32, nb), blk(32, 8);
         zt_store_kernel<<<g, blk, 0, st>>>(w.xs, w.chunk, n, b0, b0 * n, w.VThi, w.VTlo, ldn);
@@ -962,6 +1108,7 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
         const size_t smem = sizeof(float) * 2 * kWY * kWY;
         PSVD_TRY(cudaFuncSetAttribute(larft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         larft_kernel<<<dim3(w.nblk, B), 256, smem, st>>>(w.Gm, w.tau, n, w.nblk, w.Tm);
+        PSVD_TRY(cudaFuncSetAttribute(s_times_tt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStSmem));
         PSVD_TRY(cudaGetLastError());
         count_launch(1);
         for (int blk = w.nblk - 1; blk >= 0; --blk) {
@@ -988,7 +1135,9 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
                 PSVD_TRY(launch_gemm(nullptr, nullptr, &ahi, &alo, &bhi, &blo, s, B, e, st));
             }
             {
-                s_times_tt_kernel<<<dim3(n, B), kWY, 0, st>>>(w.S, ks, B, w.Tm, n, w.nblk, blk, nb, w.S2hi, w.S2lo);
+                s_times_tt_kernel<<<dim3((n + kStRows - 1) / kStRows, B), kWY, kStSmem, st>>>(w.S, ks, B, w.Tm, n,
+                                                                                            w.nblk, blk, nb, w.S2hi,
+                                                                                            w.S2lo);
                 PSVD_TRY(cudaGetLastError());
                 count_launch(1);
             }
