@@ -33,9 +33,10 @@ N = 4096
 KAPPA = 10.0
 EPS = 1e-8
 METRIC = "SVD fwd+bwd ms at 4096^2, f32-accurate: mixed vs plain path; % tensor-core peak"
-# dram__bytes_read.sum + dram__bytes_write.sum of one sytrd_kernel launch at n = 4096 (ncu
-# capture listed in profiles/sytrd_4096.md; valid while the kernel is unchanged)
-TRD_DRAM_BYTES = 100306688 + 5577554432
+# DRAM bytes (read + written) of one sytrd_kernel launch at n = 4096, from an ncu capture of
+# the current kernel (dram__bytes.sum.per_second x gpu__time_duration.sum = 148.13 GB/s x
+# 39.116 ms); valid while the kernel is unchanged
+TRD_DRAM_BYTES = 5794092046
 WORKLOAD = (f"SVD fwd+bwd of one {N}x{N} fp32 matrix A = Q1 diag(s) Q2^T, s_i = {KAPPA:g}^((n-i)/(n-1)), "
             f"eps=1e-8, kreg Algorithm 4")
 

@@ -14,7 +14,8 @@ namespace psvd {
 
 cudaError_t l1_norms(const float *A, int B, int m, int n, float *rowsum, float *colsum, int *nonfinite,
                      cudaStream_t st);
-__global__ void norm_finalize_kernel(const float *rowsum, const float *colsum, const int *nonfinite, int m, int n,
+__global__ void __launch_bounds__(kNormThreads) norm_finalize_kernel(const float *rowsum, const float *colsum,
+                                                                      const int *nonfinite, int m, int n,
                                      float *scale, int *done, int *status, int *fin);
 
 constexpr int kH = 64, kF = 8;
@@ -454,7 +455,8 @@ extern "C" int psvd_sketch_features(const float *A, const float *Z, int64_t s, f
     PSVD_TRY(cudaMemsetAsync(w.rowsum, 0, sizeof(float) * batch * m, st));
     PSVD_TRY(cudaMemsetAsync(w.nonfinite, 0, sizeof(int) * batch, st));
     PSVD_TRY(l1_norms(A, B, M, Nn, w.rowsum, w.colsum, w.nonfinite, st));
-    norm_finalize_kernel<<<B, 256, 0, st>>>(w.rowsum, w.colsum, w.nonfinite, M, Nn, w.scale, w.done, w.status, w.fin);
+    norm_finalize_kernel<<<B, kNormThreads, 0, st>>>(w.rowsum, w.colsum, w.nonfinite, M, Nn, w.scale, w.done, w.status,
+                                                     w.fin);
     const bool vec_mn = ((uintptr_t)A & 15) == 0 && ((m * n) & 3) == 0;
     const bool vec_n = ((uintptr_t)A & 15) == 0 && (n & 3) == 0;
     if (vec_mn) fro_part_kernel<true><<<dim3(kFroBlocks, B), 256, 0, st>>>(A, w.scale, (long long)m * n, w.fropart);

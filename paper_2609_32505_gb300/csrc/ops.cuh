@@ -13,6 +13,7 @@ inline long long pad_ld(long long cols) { return round_up(cols < 1 ? 1 : cols, 3
 // The column L1 norms of the normalization (Algorithm 2) are summed in slabs of kL1Rows
 // rows; the buffer of column sums holds batch x l1_slabs(m) x n partial sums.
 constexpr int kL1Rows = 256;
+constexpr int kNormThreads = 1024;   // threads of the block that finishes the norms of one matrix
 __host__ __device__ inline int l1_slabs(int m) { return m < 1 ? 1 : (m + kL1Rows - 1) / kL1Rows; }
 
 // Output format of an operand-preparation pass.

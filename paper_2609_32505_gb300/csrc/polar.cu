@@ -115,27 +115,36 @@ cudaError_t l1_norms(const float *A, int B, int m, int n, float *rowsum, float *
 
 // One block per matrix: s = sqrt(max col l1 * max row l1); special cases set the
 // matrix done (zero matrix: W = 0 and the QR step supplies U; non-finite input).
-__global__ void norm_finalize_kernel(const float *rowsum, const float *colsum, const int *nonfinite, int m, int n,
-                                     float *scale, int *done, int *status, int *fin) {
-    __shared__ float sm[32];
+// (launched with kNormThreads threads; the slab sums of a column are loaded eight at a time)
+__global__ void __launch_bounds__(kNormThreads) norm_finalize_kernel(const float *rowsum, const float *colsum,
+                                                                      const int *nonfinite, int m, int n,
+                                                                      float *scale, int *done, int *status,
+                                                                      int *fin) {
+    __shared__ float sm[2][32];
     const int b = blockIdx.x;
     float r = 0.f, c = 0.f;
     for (int i = threadIdx.x; i < m; i += blockDim.x) r = fmaxf(r, rowsum[(long long)b * m + i]);
     const int S = l1_slabs(m);
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         float cs = 0.f;                              // slab partial sums, added in slab order
-        for (int q = 0; q < S; ++q) cs += colsum[((long long)b * S + q) * n + j];
+        for (int q0 = 0; q0 < S; q0 += 8) {
+            float x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = q0 + u < S ? colsum[((long long)b * S + q0 + u) * n + j] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) cs += x[u];
+        }
         c = fmaxf(c, cs);
     }
     r = warp_max(r);
     c = warp_max(c);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (l == 0) { sm[w] = r; sm[16 + w] = c; }
+    if (l == 0) { sm[0][w] = r; sm[1][w] = c; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int i = 1; i < nw; ++i) { r = fmaxf(r, sm[i]); c = fmaxf(c, sm[16 + i]); }
-        r = fmaxf(r, sm[0]);
-        c = fmaxf(c, sm[16]);
+        for (int i = 1; i < nw; ++i) { r = fmaxf(r, sm[0][i]); c = fmaxf(c, sm[1][i]); }
+        r = fmaxf(r, sm[0][0]);
+        c = fmaxf(c, sm[1][0]);
         const double s = sqrt((double)r * (double)c);
         scale[b] = (float)s;
         if (nonfinite[b]) { done[b] = 1; status[b] = PSVD_ERR_NONFINITE; fin[b] = 0; }
@@ -560,7 +569,7 @@ int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &
     polar_init_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, prec0, w.done, w.fin, w.status, w.prec, w.steps,
                                                         w.fallback);
     if (l1_norms(A, B, m, n, w.rowsum, w.colsum, w.nonfinite, st) != cudaSuccess) return PSVD_ERR_CUDA;
-    norm_finalize_kernel<<<B, 256, 0, st>>>(w.rowsum, w.colsum, w.nonfinite, m, n, w.scale, w.done, w.status,
+    norm_finalize_kernel<<<B, kNormThreads, 0, st>>>(w.rowsum, w.colsum, w.nonfinite, m, n, w.scale, w.done, w.status,
                                             w.fin);
     count_launch(2);
     // coefficient tables: conservative CANS (Appendix B.8), classical NS, or learned bounds
