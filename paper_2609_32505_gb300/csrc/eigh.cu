@@ -967,6 +967,110 @@ __global__ void __launch_bounds__(kWY) s_times_tt_kernel(const float *S, int ks,
     }
 }
 
+// Two compact-WY blocks in one update (b = a block, a = the block above it, applied first):
+//   M (I - Y_a T_a^T Y_a^T)(I - Y_b T_b^T Y_b^T) = M - S2_a Y_a^T - S2_b Y_b^T,
+//   S2_a = S_a T_a^T,  S2_b = (S_b' - S2_a G_ab) T_b^T,
+// with S_a = M Y_a and S_b' = M Y_b from one product (S: columns [0, kWY) block b, [kWY, 2 kWY)
+// block a, the sum of ks K-split slices) and G_ab = Y_a^T Y_b.  S2 gets the same column order.
+// One block of 2 kWY threads per kPrRows rows (each thread one column of half the rows):
+// T_a, T_b and G_ab staged in shared memory with rows padded to kWY + 1 floats (thread j
+// reads row j of T, column j of G).
+constexpr int kPrRows = 16, kPrLd = kWY + 1;
+constexpr size_t kPrSmem =
+    sizeof(float) * (3 * (size_t)kWY * kPrLd + (size_t)kPrRows * 2 * kWY + (size_t)kPrRows * kWY);
+__global__ void __launch_bounds__(2 * kWY) s_pair_kernel(const float *S, int ks, int B, const float *Tm,
+                                                          const float *Gab, int n, int nblk, int npair, int blk_b,
+                                                          int q, int nb_a, float *S2hi, float *S2lo) {
+    extern __shared__ float psm[];
+    float *Ta = psm, *Tb = Ta + kWY * kPrLd, *G = Tb + kWY * kPrLd;
+    float *sr = G + kWY * kPrLd;                      // [kPrRows][2 kWY]: S rows, then S_b in place
+    float *s2a = sr + kPrRows * 2 * kWY;              // [kPrRows][kWY]
+    const int i0 = blockIdx.x * kPrRows, b = blockIdx.y, t = threadIdx.x;
+    // the three kWY x kWY matrices (16-byte aligned rows) as float4 loads, eight in flight
+#pragma unroll
+    for (int mtx = 0; mtx < 3; ++mtx) {
+        const float *src = mtx == 0 ? Tm + ((long long)b * nblk + blk_b + 1) * kWY * kWY
+                         : mtx == 1 ? Tm + ((long long)b * nblk + blk_b) * kWY * kWY
+                                    : Gab + ((long long)b * npair + q) * kWY * kWY;
+        const float4 *g4 = reinterpret_cast<const float4 *>(src);
+        float *dst = psm + mtx * kWY * kPrLd;
+        for (int q0 = t; q0 < kWY * kWY / 4; q0 += 8 * 2 * kWY) {
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                v[u] = q0 + u * 2 * kWY < kWY * kWY / 4 ? g4[q0 + u * 2 * kWY] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = 4 * (q0 + u * 2 * kWY);
+                if (e >= kWY * kWY) break;
+                float *d = dst + (e / kWY) * kPrLd + e % kWY;
+                d[0] = v[u].x; d[1] = v[u].y; d[2] = v[u].z; d[3] = v[u].w;
+            }
+        }
+    }
+    const long long slice = (long long)B * n * 2 * kWY;
+#pragma unroll
+    for (int r = 0; r < kPrRows; ++r) {
+        const int i = i0 + r;
+        float sv = 0.f;
+        if (i < n) {
+            const long long o = ((long long)b * n + i) * 2 * kWY + t;
+            float x[kBtSplit];
+#pragma unroll
+            for (int c = 0; c < kBtSplit; ++c) x[c] = c < ks ? S[c * slice + o] : 0.f;
+            sv = x[0];
+#pragma unroll
+            for (int c = 1; c < kBtSplit; ++c) if (c < ks) sv += x[c];
+        }
+        sr[r * 2 * kWY + t] = sv;
+    }
+    __syncthreads();
+    // every phase: thread t takes column j = t % kWY of the kPrRows / 2 rows of half t / kWY
+    constexpr int kH = kPrRows / 2;
+    const int j = t % kWY, rh = (t / kWY) * kH;
+    float acc[kH];
+#pragma unroll
+    for (int r = 0; r < kH; ++r) acc[r] = 0.f;
+    for (int l = j; l < nb_a; ++l) {                 // S2_a = S_a T_a^T
+        const float tv = Ta[j * kPrLd + l];
+#pragma unroll
+        for (int r = 0; r < kH; ++r) acc[r] += sr[(rh + r) * 2 * kWY + kWY + l] * tv;
+    }
+#pragma unroll
+    for (int r = 0; r < kH; ++r) s2a[(rh + r) * kWY + j] = acc[r];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kH; ++r) acc[r] = sr[(rh + r) * 2 * kWY + j];
+    for (int l = 0; l < nb_a; ++l) {                 // S_b = S_b' - S2_a G_ab
+        const float gv = G[l * kPrLd + j];
+#pragma unroll
+        for (int r = 0; r < kH; ++r) acc[r] -= s2a[(rh + r) * kWY + l] * gv;
+    }
+#pragma unroll
+    for (int r = 0; r < kH; ++r) sr[(rh + r) * 2 * kWY + j] = acc[r];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kH; ++r) acc[r] = 0.f;
+    for (int l = j; l < kWY; ++l) {                  // S2_b = S_b T_b^T (block b is full)
+        const float tv = Tb[j * kPrLd + l];
+#pragma unroll
+        for (int r = 0; r < kH; ++r) acc[r] += sr[(rh + r) * 2 * kWY + l] * tv;
+    }
+#pragma unroll
+    for (int r = 0; r < kH; ++r) {
+        const int i = i0 + rh + r;
+        if (i >= n) break;
+        const long long o = ((long long)b * n + i) * 2 * kWY;
+        float h, lo;
+        split_tf32(acc[r], h, lo);
+        S2hi[o + j] = h;
+        S2lo[o + j] = lo;
+        split_tf32(s2a[(rh + r) * kWY + j], h, lo);
+        S2hi[o + kWY + j] = h;
+        S2lo[o + kWY + j] = lo;
+    }
+}
+
 // sign convention + outputs: each row of V^T flipped so its largest-|.| entry is positive
 __global__ void eig_finalize_kernel(float *VThi, float *VTlo, long long ldn, int n, const double *lam, float *S,
                                     float *VT) {
@@ -1112,7 +1216,11 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
         PSVD_TRY(cudaFuncSetAttribute(s_times_tt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStSmem));
         PSVD_TRY(cudaGetLastError());
         count_launch(1);
-        for (int blk = w.nblk - 1; blk >= 0; --blk) {
+        // The blocks are applied in pairs (s_pair_kernel): one V^T Y product of width 2 kWY and
+        // one update with K = 2 kWY per pair halve the read-modify-write passes over V^T.
+        // With an odd count the lowest block (blk 0) goes last on its own.
+        const int first = w.nblk & 1, npair = w.nblk / 2;
+        auto single = [&](int blk) -> int {
             const int k0 = blk * kWY;
             const int nb = std::min(kWY, n - 2 - k0);
             const int r0 = ((k0 + 1) / 32) * 32;
@@ -1156,7 +1264,69 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
                 e.bs = (long long)n * ldn;
                 PSVD_TRY(launch_gemm(nullptr, nullptr, &ahi, &alo, &bhi, &blo, s, B, e, st));
             }
+            return PSVD_OK;
+        };
+        if (npair > 0) {
+            // G_ab = Y_a^T Y_b of every pair (a = b + 1): Householder rows of the two blocks
+            for (int b = 0; b < B; ++b) {
+                const float *hb = w.Vhi + b * np, *lb = w.Vlo + b * np;
+                const long long ps = (long long)2 * kWY * ldn;
+                MatView ah = view_of(hb + (long long)(first + 1) * kWY * ldn, kWY, n, ldn, ps, npair);
+                MatView al = view_of(lb + (long long)(first + 1) * kWY * ldn, kWY, n, ldn, ps, npair);
+                MatView bh = view_of(hb + (long long)first * kWY * ldn, kWY, n, ldn, ps, npair);
+                MatView bl = view_of(lb + (long long)first * kWY * ldn, kWY, n, ldn, ps, npair);
+                GemmShape s;
+                memset(&s, 0, sizeof(s));
+                s.M = kWY; s.N = kWY; s.K = n; s.prec_uniform = PREC_TF32X3; s.err = w.err;
+                EpiStore e = epi_store_plain(w.Gab + (long long)b * npair * kWY * kWY, kWY, (long long)kWY * kWY,
+                                             kWY, kWY);
+                PSVD_TRY(launch_gemm(nullptr, nullptr, &ah, &al, &bh, &bl, s, npair, e, st));
+            }
+            PSVD_TRY(cudaFuncSetAttribute(s_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPrSmem));
         }
+        for (int q = npair - 1; q >= 0; --q) {
+            const int blk_b = first + 2 * q;
+            const int k0 = blk_b * kWY;
+            const int nb_a = std::min(kWY, n - 2 - (k0 + kWY));
+            const int W = kWY + nb_a;
+            const int r0 = ((k0 + 1) / 32) * 32;
+            const int Lr = n - r0;
+            int ks = 1;
+            // S = V^T[:, r0:] [Y_b Y_a][r0:, :]   (n x W), as ks partial sums over K
+            {
+                MatView ahi = view_of(w.VThi + r0, n, Lr, ldn, (long long)n * ldn, B);
+                MatView alo = view_of(w.VTlo + r0, n, Lr, ldn, (long long)n * ldn, B);
+                MatView bhi = view_of(w.Vhi + (long long)k0 * ldn + r0, W, Lr, ldn, (long long)w.nrp * ldn, B);
+                MatView blo = view_of(w.Vlo + (long long)k0 * ldn + r0, W, Lr, ldn, (long long)w.nrp * ldn, B);
+                GemmShape s;
+                memset(&s, 0, sizeof(s));
+                s.M = n; s.N = W; s.K = Lr; s.prec_uniform = PREC_TF32X3; s.err = w.err;
+                const int tiles = ((n + kBM - 1) / kBM) * B;
+                s.ksplit = std::max(1, std::min(std::min(kBtSplit, (num_sms() + tiles - 1) / tiles), Lr / 128));
+                ks = s.ksplit;
+                EpiStore e = epi_store_plain(w.S, 2 * kWY, (long long)n * 2 * kWY, n, W);
+                PSVD_TRY(launch_gemm(nullptr, nullptr, &ahi, &alo, &bhi, &blo, s, B, e, st));
+            }
+            s_pair_kernel<<<dim3((n + kPrRows - 1) / kPrRows, B), 2 * kWY, kPrSmem, st>>>(
+                w.S, ks, B, w.Tm, w.Gab, n, w.nblk, npair, blk_b, q, nb_a, w.S2hi, w.S2lo);
+            PSVD_TRY(cudaGetLastError());
+            count_launch(1);
+            // V^T[:, r0:] -= S2 [Y_b Y_a][r0:, :]^T
+            {
+                MatView ahi = view_of(w.S2hi, n, W, 2 * kWY, (long long)n * 2 * kWY, B);
+                MatView alo = view_of(w.S2lo, n, W, 2 * kWY, (long long)n * 2 * kWY, B);
+                MatView bhi = view_of(w.Yhi + (long long)r0 * ldn + k0, Lr, W, ldn, (long long)n * ldn, B);
+                MatView blo = view_of(w.Ylo + (long long)r0 * ldn + k0, Lr, W, ldn, (long long)n * ldn, B);
+                GemmShape s;
+                memset(&s, 0, sizeof(s));
+                s.M = n; s.N = Lr; s.K = W; s.prec_uniform = PREC_TF32X3; s.err = w.err;
+                EpiSubSplit e;
+                e.rows = n; e.cols = Lr; e.hi = w.VThi + r0; e.lo = w.VTlo + r0; e.ld = ldn;
+                e.bs = (long long)n * ldn;
+                PSVD_TRY(launch_gemm(nullptr, nullptr, &ahi, &alo, &bhi, &blo, s, B, e, st));
+            }
+        }
+        if (first) PSVD_TRY_RC(single(0));
     }
     eig_finalize_kernel<<<dim3(n, B), 128, 0, st>>>(w.VThi, w.VTlo, ldn, n, w.lam, S, VT);
     count_launch(1);

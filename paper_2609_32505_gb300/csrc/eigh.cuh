@@ -21,10 +21,11 @@ struct EighWS {
     float *Vhi = nullptr, *Vlo = nullptr;      // Householder rows split (n x ldn)
     float *Yhi = nullptr, *Ylo = nullptr;      // Householder vectors as columns (n x ldn)
     float *VThi = nullptr, *VTlo = nullptr;    // current V^T split (n x ldn)
-    float *S = nullptr;                        // V^T Y for one block (n x kWY)
-    float *S2hi = nullptr, *S2lo = nullptr;    // S T^T split (n x kWY)
+    float *S = nullptr;                        // V^T Y for a pair of blocks (n x 2 kWY), K-split slices
+    float *S2hi = nullptr, *S2lo = nullptr;    // the pair's S2 split (n x 2 kWY)
     float *Tm = nullptr;                       // [B][nblk][kWY][kWY]
     float *Gm = nullptr;                       // [B][nblk][kWY][kWY]  Y^T Y per block
+    float *Gab = nullptr;                      // [B][nblk/2][kWY][kWY]  Y_a^T Y_b per pair of blocks
     double *xs = nullptr;                      // inverse-iteration vectors, interleaved [n][chunk]
     double *u0 = nullptr, *u1 = nullptr, *u2 = nullptr, *lm = nullptr;
     unsigned *piv = nullptr;            // pivot bits, [ceil(n/32)][chunk]
@@ -54,11 +55,12 @@ struct EighWS {
         Ylo = cv.template take<float>(B64 * nn);
         VThi = cv.template take<float>(B64 * nn);
         VTlo = cv.template take<float>(B64 * nn);
-        S = cv.template take<float>(kBtSplit * B64 * n * kWY);
-        S2hi = cv.template take<float>(B64 * n * kWY);
-        S2lo = cv.template take<float>(B64 * n * kWY);
+        S = cv.template take<float>(kBtSplit * B64 * n * 2 * kWY);
+        S2hi = cv.template take<float>(B64 * n * 2 * kWY);
+        S2lo = cv.template take<float>(B64 * n * 2 * kWY);
         Tm = cv.template take<float>(B64 * (nblk > 0 ? nblk : 1) * kWY * kWY);
         Gm = cv.template take<float>(B64 * (nblk > 0 ? nblk : 1) * kWY * kWY);
+        Gab = cv.template take<float>(B64 * (nblk > 1 ? nblk / 2 : 1) * kWY * kWY);
         xs = cv.template take<double>((long long)n * chunk);
         u0 = cv.template take<double>((long long)n * chunk);
         u1 = cv.template take<double>((long long)n * chunk);

@@ -407,16 +407,30 @@ __global__ void polar_finalize_kernel(int m, int n, int B, const int *fin, const
     }
 }
 
-// H = (Hraw + Hraw^T) / 2 in FP64, stored FP32 (Hsym, and H_out when given).
-__global__ void symmetrize_kernel(const float *Hraw, int n, float *Hsym, float *Hout) {
-    const int b = blockIdx.z;
-    const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
-    if (i >= n || j >= n) return;
+// H = (Hraw + Hraw^T) / 2, stored FP32 (Hsym, and H_out when given).
+__global__ void __launch_bounds__(256) symmetrize_kernel(const float *Hraw, int n, float *Hsym, float *Hout) {
+    // One 32 x 32 tile per block (32 x 8 threads), its mirror tile staged in shared memory so
+    // that both reads are coalesced.  (h_ij + h_ji) / 2 is formed as the FP32 sum scaled by
+    // 1/2: the scaling is exact, so the result equals the FP64 average rounded to FP32 (the
+    // FP64 symmetrization) except where the average is subnormal.
+    __shared__ float tm[32][33];
+    const int b = blockIdx.z, i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
     const float *h = Hraw + (long long)b * n * n;
-    const double v = 0.5 * ((double)h[(long long)i * n + j] + (double)h[(long long)j * n + i]);
-    const long long o = (long long)b * n * n + (long long)i * n + j;
-    Hsym[o] = (float)v;
-    if (Hout) Hout[o] = (float)v;
+#pragma unroll
+    for (int r = ty; r < 32; r += 8)
+        tm[r][tx] = (j0 + r < n && i0 + tx < n) ? h[(long long)(j0 + r) * n + i0 + tx] : 0.f;
+    __syncthreads();
+#pragma unroll
+    for (int r = ty; r < 32; r += 8) {
+        const int i = i0 + r, j = j0 + tx;
+        if (i < n && j < n) {
+            const long long o = (long long)b * n * n + (long long)i * n + j;
+            const float v = __fmul_rn(__fadd_rn(h[(long long)i * n + j], tm[tx][r]), 0.5f);
+            Hsym[o] = v;
+            if (Hout) Hout[o] = v;
+        }
+    }
 }
 
 // hist[k * B + b] = ||G_k - I||_F / sqrt(n) at the Gram of step k (0 where the matrix had
@@ -646,8 +660,7 @@ int polar_forward(const float *A, float *W, float *H_out, bool want_h, PolarWS &
         s.M = n; s.N = n; s.K = m; s.prec_uniform = PREC_TF32X3; s.err = w.err;
         EpiStore e = epi_store_plain(w.Hraw, n, (long long)n * n, n, n);
         if (launch_gemm(nullptr, nullptr, &ahi, &alo, &bhi, &blo, s, B, e, st) != cudaSuccess) return PSVD_ERR_CUDA;
-        dim3 g((n + 15) / 16, (n + 15) / 16, B), blk(16, 16);
-        symmetrize_kernel<<<g, blk, 0, st>>>(w.Hraw, n, w.Hsym, H_out);
+        symmetrize_kernel<<<dim3((n + 31) / 32, (n + 31) / 32, B), dim3(32, 8), 0, st>>>(w.Hraw, n, w.Hsym, H_out);
         count_launch(1);
     }
     if (info) {
