@@ -486,6 +486,15 @@ def main():
         reports["schedule_comparison"] = sc
     except Exception as exc:
         reports["schedule_comparison_error"] = f"{type(exc).__name__}: {exc}"
+    # the learned schedule at the size of its study: 2048 held-out 1024^2 matrices of the three
+    # training families, conservative vs learned (steps, device time, final residual); ~1 min,
+    # most of it generating the inputs
+    if rank == 0:
+        try:
+            from paper_2609_32505_gb300 import train_schedule
+            reports["learned_eval"] = train_schedule.evaluate(2048, quiet=True)
+        except Exception as exc:
+            reports["learned_eval_error"] = f"{type(exc).__name__}: {exc}"
 
     if rank == 0:
         line = {"metric": METRIC, "value": ms_mixed, "unit": "ms", "n_gpus": ws, "steps": args.steps,

@@ -572,21 +572,34 @@ PSVD_DEV void cp_async8(double *sdst, const double *gsrc) {
 PSVD_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 PSVD_DEV void cp_async_wait_ring() { asm volatile("cp.async.wait_group %0;" ::"n"(kIvR - 2) : "memory"); }
 
-// Streams `nsteps` rows: addr(k, a) gives the global address of array a at step k (or
-// nullptr), body(k, ring slot pointer) consumes them in order; slot(a) = p + a*kIvJ*32.
-template <class Addr, class Body>
-PSVD_DEV void iv_stream(double *ring, int nsteps, int na, Addr addr, Body body) {
+// One streamed operand: row k lives at p + k * stride (p already at row 0; stride may be
+// negative), rows k in [kmin, kmax) exist, the others are not fetched (their slots are
+// left as they are and the body does not read them).
+struct IvArr {
+    const double *p;
+    long long stride;
+    int kmin, kmax;
+};
+
+// Streams `nsteps` rows of NA operands through the ring; body(k, ring slot pointer) consumes
+// them in order, slot(a) = p + a*kIvJ*32.  The issuing walks one pointer per operand, so a
+// row costs an add, a copy and a shared address per operand.
+template <int NA, class Body>
+PSVD_DEV void iv_stream(double *ring, int nsteps, const IvArr (&arr)[NA], Body body) {
     const int lane = threadIdx.x & 31;
     const int nst = (nsteps + kIvJ - 1) / kIvJ;
+    const double *next[NA];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) next[a] = arr[a].p;
+    int kn = 0;                                    // row the pointers stand at
     auto issue = [&](int st) {
         if (st < nst) {
-            double *buf = ring + (st % kIvR) * kIvStage;
-            for (int jj = 0; jj < kIvJ; ++jj) {
-                const int k = st * kIvJ + jj;
-                if (k >= nsteps) break;
-                for (int a = 0; a < na; ++a) {
-                    const double *g = addr(k, a);
-                    if (g) cp_async8(buf + (a * kIvJ + jj) * kIvW + lane, g);
+            double *buf = ring + (st % kIvR) * kIvStage + lane;
+            for (int jj = 0; jj < kIvJ && kn < nsteps; ++jj, ++kn) {
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    if (kn >= arr[a].kmin && kn < arr[a].kmax) cp_async8(buf + (a * kIvJ + jj) * kIvW, next[a]);
+                    next[a] += arr[a].stride;
                 }
             }
         }
@@ -617,10 +630,8 @@ PSVD_DEV void iv_factor(const InvitParams &P, double *ring, const double *D, con
     double a = D[0] - mu;
     double bsup = E[0];
     unsigned word = 0;
-    iv_stream(ring, n - 1, 3,
-              [&](int j, int q) -> const double * {
-                  return q == 0 ? D + j + 1 : (q == 1 ? E + j : (j + 1 < n - 1 ? E + j + 1 : nullptr));
-              },
+    const IvArr arr[3] = {{D + 1, 1, 0, n - 1}, {E, 1, 0, n - 1}, {E + 1, 1, 0, n - 2}};
+    iv_stream(ring, n - 1, arr,
               [&](int j, const double *p) {
                   const double c = IV_SLOT(p, 1);
                   const double dn = IV_SLOT(p, 0) - mu;
@@ -655,10 +666,8 @@ PSVD_DEV void iv_forward(const InvitParams &P, double *ring, int n, int t, int i
     double carry = first ? iv_start(i, 0) : x[t] * scale;
     unsigned pword = 0;
     unsigned pnext = P.piv[t];
-    iv_stream(ring, n - 1, 2,
-              [&](int j, int q) -> const double * {
-                  return q == 0 ? (first ? nullptr : x + (long long)(j + 1) * s + t) : P.lm + (long long)j * s + t;
-              },
+    const IvArr arr[2] = {{x + s + t, s, 0, first ? 0 : n - 1}, {P.lm + t, s, 0, n - 1}};
+    iv_stream(ring, n - 1, arr,
               [&](int j, const double *p) {
                   if ((j & 31) == 0) {
                       pword = pnext;
@@ -682,11 +691,10 @@ PSVD_DEV double iv_backward(const InvitParams &P, double *ring, int n, int t) {
     double x1 = x[last] * P.u0[last], x2 = 0.0;
     x[last] = x1;
     double nrm = x1 * x1;
-    iv_stream(ring, n - 1, 4,
-              [&](int k, int q) -> const double * {
-                  const long long o = (long long)(n - 2 - k) * s + t;
-                  return q == 0 ? x + o : (q == 1 ? P.u0 + o : (q == 2 ? P.u1 + o : P.u2 + o));
-              },
+    const long long o0 = (long long)(n - 2) * s + t;     // row n - 2 - k at step k
+    const IvArr arr[4] = {{x + o0, -s, 0, n - 1}, {P.u0 + o0, -s, 0, n - 1}, {P.u1 + o0, -s, 0, n - 1},
+                          {P.u2 + o0, -s, 0, n - 1}};
+    iv_stream(ring, n - 1, arr,
               [&](int k, const double *p) {
                   const double v = (IV_SLOT(p, 0) - IV_SLOT(p, 2) * x1 - IV_SLOT(p, 3) * x2) * IV_SLOT(p, 1);
                   x[(long long)(n - 2 - k) * s + t] = v;
@@ -703,10 +711,8 @@ PSVD_DEV double iv_finish(const InvitParams &P, double *ring, const double *D, c
     const long long s = P.stride;
     double *x = P.xs;
     double r = 0.0, prev = 0.0;
-    iv_stream(ring, n, 3,
-              [&](int j, int q) -> const double * {
-                  return q == 0 ? x + (long long)j * s + t : (q == 1 ? D + j : (j > 0 ? E + j - 1 : nullptr));
-              },
+    const IvArr arr[3] = {{x + t, s, 0, n}, {D, 1, 0, n}, {E - 1, 1, 1, n}};   // E[j - 1] from j = 1 on
+    iv_stream(ring, n, arr,
               [&](int j, const double *p) {
                   const double xj = IV_SLOT(p, 0) * scale;
                   x[(long long)j * s + t] = xj;

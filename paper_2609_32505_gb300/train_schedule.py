@@ -113,7 +113,7 @@ def main(argv=None):
           f"held-out median |log error| {resid.median().item():.3f}, margin {margin:.3f} -> {a.out}")
 
 
-def evaluate(count: int, n: int = 1024, chunk: int = 64, path: str = DEFAULT_OUT):
+def evaluate(count: int, n: int = 1024, chunk: int = 64, path: str = DEFAULT_OUT, quiet: bool = False):
     """Held-out matrices of the three families (seeds 400, 401, ...): steps and device time of
     the conservative and the learned schedule (bound prediction included), same tolerance."""
     dev = torch.device("cuda")
@@ -130,6 +130,7 @@ def evaluate(count: int, n: int = 1024, chunk: int = 64, path: str = DEFAULT_OUT
         torch.cuda.synchronize()
         return r, e0.elapsed_time(e1)
 
+    ortho_c, ortho_l = [], []
     for c in range(0, count, chunk):
         seeds = list(range(400 + c, 400 + min(count, c + chunk)))
         A = family_batch(seeds, n, dev)
@@ -149,11 +150,21 @@ def evaluate(count: int, n: int = 1024, chunk: int = 64, path: str = DEFAULT_OUT
             n_fb += b["sched_fallback"]
             steps_c.append(a["iters"])
             steps_l.append(b["iters"])
+            ortho_c.append(a["ortho_resid"])
+            ortho_l.append(b["ortho_resid"])
         del A
-    print(f"{count} matrices of {n} x {n}: {n_ok} converged under the conservative schedule ({n_fail} hit the "
-          f"cap); mean steps conservative {np.mean(steps_c):.2f}, learned {np.mean(steps_l):.2f} "
-          f"({n_fb} conservative reruns); device time conservative {tot['cons_ms']:.1f} ms, learned "
-          f"{tot['learn_ms']:.1f} ms + bound prediction {tot['pred_ms']:.1f} ms")
+    res = {"matrices": count, "n": n, "converged": n_ok, "hit_cap": n_fail,
+           "mean_steps_conservative": float(np.mean(steps_c)), "mean_steps_learned": float(np.mean(steps_l)),
+           "conservative_reruns": int(n_fb), "device_ms_conservative": tot["cons_ms"],
+           "device_ms_learned": tot["learn_ms"], "device_ms_bound_prediction": tot["pred_ms"],
+           "max_ortho_resid_conservative": float(np.max(ortho_c)), "max_ortho_resid_learned": float(np.max(ortho_l))}
+    if not quiet:
+        print(f"{count} matrices of {n} x {n}: {n_ok} converged under the conservative schedule ({n_fail} hit the "
+              f"cap); mean steps conservative {res['mean_steps_conservative']:.2f}, learned "
+              f"{res['mean_steps_learned']:.2f} ({n_fb} conservative reruns); device time conservative "
+              f"{tot['cons_ms']:.1f} ms, learned {tot['learn_ms']:.1f} ms + bound prediction {tot['pred_ms']:.1f} ms; "
+              f"largest final residual {res['max_ortho_resid_conservative']:.2e} / {res['max_ortho_resid_learned']:.2e}")
+    return res
 
 
 def load(path: str = DEFAULT_OUT, device="cuda"):
