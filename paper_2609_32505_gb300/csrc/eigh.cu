@@ -877,7 +877,7 @@ __global__ void zt_store_kernel(const double *xs, long long stride, int n, int f
 
 // ------------------------------------------------------------ back-transform
 // Upper-triangular T of the forward compact-WY form H_k0 ... H_k1-1 = I - Y T Y^T, one
-// block per (WY block, matrix), from G = Y^T Y (computed on the tensor cores):
+// block per (WY block, matrix), from G = Y^T Y (computed on the tensor cores, symmetric):
 // T[c][c] = tau_c,  T[:c, c] = -tau_c T[:c, :c] G[:c, c].
 __global__ void larft_kernel(const float *Gm, const float *tau, int n, int nblk, float *Tm) {
     extern __shared__ float sm2[];
@@ -891,15 +891,17 @@ __global__ void larft_kernel(const float *Gm, const float *tau, int n, int nblk,
     const float *tb = tau + (long long)b * n + k0;
     if (threadIdx.x == 0) T[0] = tb[0];
     __syncthreads();
+    // column c: entry a (< c) is a dot product over l in [a, c), one warp per entry with its
+    // lanes splitting l; G is symmetric, so its column c is read as row c (contiguous)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int c = 1; c < nb; ++c) {
         const float tc = tb[c];
-        float v = 0.f;
-        if (threadIdx.x < c) {
-            const int a = threadIdx.x;
-            for (int l = a; l < c; ++l) v += T[a * kWY + l] * G[l * kWY + c];
+        for (int a = warp; a < c; a += nw) {
+            float v = 0.f;
+            for (int l = a + lane; l < c; l += 32) v += T[a * kWY + l] * G[c * kWY + l];
+            v = warp_sum(v);
+            if (lane == 0) T[a * kWY + c] = -tc * v;
         }
-        __syncthreads();
-        if (threadIdx.x < c) T[threadIdx.x * kWY + c] = -tc * v;
         if (threadIdx.x == 0) T[c * kWY + c] = tc;
         __syncthreads();
     }
@@ -979,20 +981,24 @@ __global__ void __launch_bounds__(kWY) s_times_tt_kernel(const float *S, int ks,
 // with S_a = M Y_a and S_b' = M Y_b from one product (S: columns [0, kWY) block b, [kWY, 2 kWY)
 // block a, the sum of ks K-split slices) and G_ab = Y_a^T Y_b.  S2 gets the same column order.
 // One block of 2 kWY threads per kPrRows rows (each thread one column of half the rows):
-// T_a, T_b and G_ab staged in shared memory with rows padded to kWY + 1 floats (thread j
-// reads row j of T, column j of G).
-constexpr int kPrRows = 16, kPrLd = kWY + 1;
+// T_a, T_b and G_ab^T staged in shared memory with rows padded to kPrLd floats, so that a
+// thread reads 4 consecutive entries of its row as one float4 and the rows of S as float4
+// broadcasts.  T is upper triangular and zero past its block's width, and S is zeroed past
+// the pair's width, so the sums run over whole float4s.
+constexpr int kPrRows = 16, kPrLd = kWY + 4;
 constexpr size_t kPrSmem =
     sizeof(float) * (3 * (size_t)kWY * kPrLd + (size_t)kPrRows * 2 * kWY + (size_t)kPrRows * kWY);
 __global__ void __launch_bounds__(2 * kWY) s_pair_kernel(const float *S, int ks, int B, const float *Tm,
                                                           const float *Gab, int n, int nblk, int npair, int blk_b,
                                                           int q, int nb_a, float *S2hi, float *S2lo) {
-    extern __shared__ float psm[];
-    float *Ta = psm, *Tb = Ta + kWY * kPrLd, *G = Tb + kWY * kPrLd;
-    float *sr = G + kWY * kPrLd;                      // [kPrRows][2 kWY]: S rows, then S_b in place
+    extern __shared__ __align__(16) float psm[];
+    float *Ta = psm, *Tb = Ta + kWY * kPrLd, *Gt = Tb + kWY * kPrLd;
+    float *sr = Gt + kWY * kPrLd;                     // [kPrRows][2 kWY]: S rows, then S_b in place
     float *s2a = sr + kPrRows * 2 * kWY;              // [kPrRows][kWY]
     const int i0 = blockIdx.x * kPrRows, b = blockIdx.y, t = threadIdx.x;
-    // the three kWY x kWY matrices (16-byte aligned rows) as float4 loads, eight in flight
+    const int W = kWY + nb_a;
+    // the three kWY x kWY matrices (16-byte aligned rows) as float4 loads, eight in flight;
+    // G_ab is stored transposed (row j of Gt = column j of G_ab)
 #pragma unroll
     for (int mtx = 0; mtx < 3; ++mtx) {
         const float *src = mtx == 0 ? Tm + ((long long)b * nblk + blk_b + 1) * kWY * kWY
@@ -1009,8 +1015,15 @@ __global__ void __launch_bounds__(2 * kWY) s_pair_kernel(const float *S, int ks,
             for (int u = 0; u < 8; ++u) {
                 const int e = 4 * (q0 + u * 2 * kWY);
                 if (e >= kWY * kWY) break;
-                float *d = dst + (e / kWY) * kPrLd + e % kWY;
-                d[0] = v[u].x; d[1] = v[u].y; d[2] = v[u].z; d[3] = v[u].w;
+                const int r = e / kWY, c = e % kWY;
+                const float x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+                if (mtx < 2) {
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) dst[r * kPrLd + c + h] = x[h];
+                } else {
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) dst[(c + h) * kPrLd + r] = x[h];
+                }
             }
         }
     }
@@ -1019,7 +1032,7 @@ __global__ void __launch_bounds__(2 * kWY) s_pair_kernel(const float *S, int ks,
     for (int r = 0; r < kPrRows; ++r) {
         const int i = i0 + r;
         float sv = 0.f;
-        if (i < n) {
+        if (i < n && t < W) {
             const long long o = ((long long)b * n + i) * 2 * kWY + t;
             float x[kBtSplit];
 #pragma unroll
@@ -1034,33 +1047,37 @@ __global__ void __launch_bounds__(2 * kWY) s_pair_kernel(const float *S, int ks,
     // every phase: thread t takes column j = t % kWY of the kPrRows / 2 rows of half t / kWY
     constexpr int kH = kPrRows / 2;
     const int j = t % kWY, rh = (t / kWY) * kH;
+    const int na4 = (nb_a + 3) & ~3;
+    auto dot4 = [](float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; };
     float acc[kH];
 #pragma unroll
     for (int r = 0; r < kH; ++r) acc[r] = 0.f;
-    for (int l = j; l < nb_a; ++l) {                 // S2_a = S_a T_a^T
-        const float tv = Ta[j * kPrLd + l];
+    for (int l = j & ~3; l < na4; l += 4) {          // S2_a = S_a T_a^T
+        const float4 tv = *reinterpret_cast<const float4 *>(Ta + j * kPrLd + l);
 #pragma unroll
-        for (int r = 0; r < kH; ++r) acc[r] += sr[(rh + r) * 2 * kWY + kWY + l] * tv;
+        for (int r = 0; r < kH; ++r)
+            acc[r] += dot4(*reinterpret_cast<const float4 *>(sr + (rh + r) * 2 * kWY + kWY + l), tv);
     }
 #pragma unroll
     for (int r = 0; r < kH; ++r) s2a[(rh + r) * kWY + j] = acc[r];
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kH; ++r) acc[r] = sr[(rh + r) * 2 * kWY + j];
-    for (int l = 0; l < nb_a; ++l) {                 // S_b = S_b' - S2_a G_ab
-        const float gv = G[l * kPrLd + j];
+    for (int l = 0; l < na4; l += 4) {               // S_b = S_b' - S2_a G_ab
+        const float4 gv = *reinterpret_cast<const float4 *>(Gt + j * kPrLd + l);
 #pragma unroll
-        for (int r = 0; r < kH; ++r) acc[r] -= s2a[(rh + r) * kWY + l] * gv;
+        for (int r = 0; r < kH; ++r) acc[r] -= dot4(*reinterpret_cast<const float4 *>(s2a + (rh + r) * kWY + l), gv);
     }
+    __syncthreads();                                 // every thread has read S_b' before it is replaced
 #pragma unroll
     for (int r = 0; r < kH; ++r) sr[(rh + r) * 2 * kWY + j] = acc[r];
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kH; ++r) acc[r] = 0.f;
-    for (int l = j; l < kWY; ++l) {                  // S2_b = S_b T_b^T (block b is full)
-        const float tv = Tb[j * kPrLd + l];
+    for (int l = j & ~3; l < kWY; l += 4) {          // S2_b = S_b T_b^T (block b is full)
+        const float4 tv = *reinterpret_cast<const float4 *>(Tb + j * kPrLd + l);
 #pragma unroll
-        for (int r = 0; r < kH; ++r) acc[r] += sr[(rh + r) * 2 * kWY + l] * tv;
+        for (int r = 0; r < kH; ++r) acc[r] += dot4(*reinterpret_cast<const float4 *>(sr + (rh + r) * 2 * kWY + l), tv);
     }
 #pragma unroll
     for (int r = 0; r < kH; ++r) {
