@@ -133,21 +133,24 @@ struct EpiQ {
     float *hi, *lo;
     long long ld;
     struct Acc {};
+    // element path through the product kernel's shared-memory transpose, so that a warp
+    // reads G and writes hi/lo in 64-byte row segments
+    static constexpr bool kElem = true;
+    PSVD_DEV bool staged() const { return true; }
+    PSVD_DEV void elem(Acc &, int b, int r, int c, float v) const {
+        if (r >= m || c >= n) return;
+        float x = 2.f * v;
+        if (G) x += G[(long long)b * m * n + (long long)r * n + c] * dr_of(S[(long long)b * n + c], sqrt_eps, exact);
+        float h, l;
+        split_tf32(x, h, l);
+        const long long o = (long long)b * m * ld + (long long)r * ld + c;
+        hi[o] = h;
+        lo[o] = l;
+    }
     PSVD_DEV void begin(Acc &) const {}
-    PSVD_DEV void chunk(Acc &, int b, int r, int c0, int, int, float (&v)[16]) const {
-        if (r >= m) return;
+    PSVD_DEV void chunk(Acc &a, int b, int r, int c0, int, int, float (&v)[16]) const {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int c = c0 + i;
-            if (c >= n) break;
-            float x = 2.f * v[i];
-            if (G) x += G[(long long)b * m * n + (long long)r * n + c] * dr_of(S[(long long)b * n + c], sqrt_eps, exact);
-            float h, l;
-            split_tf32(x, h, l);
-            const long long o = (long long)b * m * ld + (long long)r * ld + c;
-            hi[o] = h;
-            lo[o] = l;
-        }
+        for (int i = 0; i < 16; ++i) elem(a, b, r, c0 + i, v[i]);
     }
     PSVD_DEV void finish(Acc &, int, int, int) const {}
 };
