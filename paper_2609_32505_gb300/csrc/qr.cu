@@ -62,7 +62,10 @@ struct PanelArgs {
 // and after the barrier every CTA adds the slots in rank order (so all get the same totals,
 // bit for bit) and builds the reflector redundantly: beta = -sign(alpha) sqrt(alpha^2 + s2),
 // tau = (beta - alpha) / beta, v = [1; x / (alpha - beta)].  Slots are double-buffered by
-// column parity, which makes one barrier per column enough.
+// column parity, which makes one barrier per column enough.  The slots and their sums are
+// FP32, like the partial sums they hold (FP64 sums of the cluster's 8 or 16 partials took
+// ~40% of a column's time on the narrow FP64 pipe, measured, and added no accuracy that
+// the FP32 partial sums had).
 __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(PanelArgs P) {
     cg::cluster_group cluster = cg::this_cluster();
     const int CL = P.cl, rank = (int)cluster.block_rank();
@@ -70,8 +73,9 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(PanelArgs P) {
     if (P.skip[b]) return;                       // uniform across the cluster
     extern __shared__ __align__(16) double qsm[];
     const int nb = P.nb, pw = P.pw, j0 = P.j0, m = P.m, n = P.n;
-    double *xch = qsm;                           // [2][CL][2 nb] slots, double-buffered by column parity
-    double *part = xch + 2 * CL * 2 * nb;        // [2 nb] (unused rows kept for the layout)
+    float *xch = reinterpret_cast<float *>(qsm); // [2][CL][2 nb] slots, double-buffered by column parity
+    double *part = qsm + 2 * CL * 2 * nb;        // [2 nb] doubles of room
+    float *vec = reinterpret_cast<float *>(part); // [2 nb] this CTA's vector of the column
     float *coef = reinterpret_cast<float *>(part + 4 * nb);   // [nb] f_c' of this column, then [2] scal, beta
     float *scal_s = coef + nb;
     float *red = reinterpret_cast<float *>(part + 5 * nb);    // [kQrThreads] row-block partial sums
@@ -123,33 +127,35 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(PanelArgs P) {
             if (jlp >= 0 && jlp < nr && tid == 0) xp[jlp] = scal_s[1];
         }
         __syncthreads();
-        // this CTA's vector (sum over the row blocks; the row-j values from its owner) into a
-        // slot of every CTA of the cluster
+        // this CTA's vector (sum over the row blocks; the row-j values from its owner), formed
+        // once in shared memory, then copied into a slot of every CTA of the cluster
+        for (int k = tid; k < 2 * live; k += blockDim.x) {
+            if (k < live) {
+                const int e = c + k;
+                float sum = 0.f;
+                for (int q = 0; q < nrb; ++q) sum += red[q * nb + e];
+                vec[e] = sum;
+            } else {
+                const int e = nb + c + (k - live);
+                vec[e] = own ? slab[(e - nb) * Sp + jl] : 0.f;
+            }
+        }
+        __syncthreads();
         for (int t = tid; t < CL * 2 * live; t += blockDim.x) {
             const int peer = t / (2 * live), k = t - peer * 2 * live;
-            double v;
-            int e;
-            if (k < live) {
-                e = c + k;
-                float s = 0.f;
-                for (int q = 0; q < nrb; ++q) s += red[q * nb + e];
-                v = (double)s;
-            } else {
-                e = nb + c + (k - live);
-                v = own ? (double)slab[(e - nb) * Sp + jl] : 0.0;
-            }
-            double *dst = cluster.map_shared_rank(xch + ((long long)par * CL + rank) * 2 * nb, peer);
-            dst[e] = v;
+            const int e = k < live ? c + k : nb + c + (k - live);
+            float *dst = cluster.map_shared_rank(xch + ((long long)par * CL + rank) * 2 * nb, peer);
+            dst[e] = vec[e];
         }
         cluster.sync();
         // warp 0: the cluster totals, the reflector (FP32, as single-precision Householder QR
         // computes it) and the coefficient f_c' = tau (v^T y_c') = tau (y_c',j + scal P_c')
         if (tid < 32) {
             const int lane = tid;
-            const double *slots = xch + (long long)par * CL * 2 * nb;
-            double alpha = 0.0, s2 = 0.0;
+            const float *slots = xch + (long long)par * CL * 2 * nb;
+            float alpha = 0.f, s2 = 0.f;
             for (int q = 0; q < CL; ++q) { alpha += slots[q * 2 * nb + nb + c]; s2 += slots[q * 2 * nb + c]; }
-            const float fa = (float)alpha, f2 = (float)s2;
+            const float fa = alpha, f2 = s2;
             float beta, tau, scal;
             if (f2 == 0.f) { beta = fa; tau = 0.f; scal = 0.f; }
             else {
@@ -158,9 +164,9 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(PanelArgs P) {
                 scal = 1.f / (fa - beta);
             }
             for (int k = c + 1 + lane; k < pw; k += 32) {
-                double pc = 0.0, yj = 0.0;
+                float pc = 0.f, yj = 0.f;
                 for (int q = 0; q < CL; ++q) { pc += slots[q * 2 * nb + k]; yj += slots[q * 2 * nb + nb + k]; }
-                coef[k] = tau * ((float)yj + (float)pc * scal);
+                coef[k] = tau * (yj + pc * scal);
             }
             if (lane == 0) {
                 scal_s[0] = scal;
