@@ -272,37 +272,58 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(PanelArgs P) {
 
 // W2^T[c][i] = sum_l op(T)[i][l] W[l][c], W = sum of the ks K-split slices of Y^T X; op = T^T
 // (factorization, X <- (I - Y T Y^T)^T X) or T (accumulation of Q, X <- (I - Y T Y^T) X).
-// Tm holds the nb x nb T of every (matrix, panel); one thread per column c.
-__global__ void qr_tapply_kernel(const float *Wp, int ks, int B, int nb, int pw, int n, int ncol, const float *Tm,
-                                 int npan, int panel, int trans, const int *skip, float *W2hi, float *W2lo) {
-    extern __shared__ float Ts[];
+// Tm holds the nb x nb T of every (matrix, panel).  One block of 8 warps per kTaCols columns:
+// the block's columns of W (slices summed) are staged in shared memory with coalesced loads,
+// warp g forms outputs i = g, g + 8, ... of every column (lane = column), and the block's
+// rows of W2^T (kTaCols x nb, contiguous) are written back as float4.
+constexpr int kTaCols = 32, kTaWarps = 8;
+__global__ void __launch_bounds__(32 * kTaWarps) qr_tapply_kernel(const float *Wp, int ks, int B, int nb, int pw,
+                                                                  int n, int ncol, const float *Tm, int npan,
+                                                                  int panel, int trans, const int *skip,
+                                                                  float *W2hi, float *W2lo) {
+    __shared__ float Ts[64 * 65];                   // op(T), rows padded
+    __shared__ float ws[64][kTaCols + 1];           // W[l][c] for the block's columns
+    __shared__ __align__(16) float oh[kTaCols * 64], ol[kTaCols * 64];   // W2^T rows, hi and lo
     const int b = blockIdx.y;
     if (skip[b]) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c0 = blockIdx.x * kTaCols;
     const float *T = Tm + ((long long)b * npan + panel) * nb * nb;
     for (int t = threadIdx.x; t < pw * pw; t += blockDim.x) {
         const int i = t / pw, l = t - i * pw;
-        Ts[i * pw + l] = trans ? T[l * nb + i] : T[i * nb + l];
+        Ts[i * 65 + l] = trans ? T[l * nb + i] : T[i * nb + l];
+    }
+    for (int l = warp; l < pw; l += kTaWarps) {
+        const int c = c0 + lane;
+        float sum = 0.f;
+        if (c < ncol)
+            for (int kc = 0; kc < ks; ++kc) sum += Wp[(((long long)kc * B + b) * nb + l) * n + c];
+        ws[l][lane] = sum;
     }
     __syncthreads();
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncol) return;
-    float w[64];
-#pragma unroll
-    for (int l = 0; l < 64; ++l) {
-        float s = 0.f;
-        if (l < pw)
-            for (int kc = 0; kc < ks; ++kc) s += Wp[(((long long)kc * B + b) * nb + l) * n + c];
-        w[l] = s;
-    }
-    for (int i = 0; i < pw; ++i) {
-        float s = 0.f;
-#pragma unroll
-        for (int l = 0; l < 64; ++l)
-            if (l < pw) s += Ts[i * pw + l] * w[l];
+    for (int i = warp; i < nb; i += kTaWarps) {
+        float sum = 0.f;
+        if (i < pw)
+            for (int l = 0; l < pw; ++l) sum += Ts[i * 65 + l] * ws[l][lane];
         float h, lo;
-        split_tf32(s, h, lo);
-        W2hi[((long long)b * n + c) * nb + i] = h;
-        W2lo[((long long)b * n + c) * nb + i] = lo;
+        split_tf32(sum, h, lo);
+        oh[lane * 64 + i] = h;
+        ol[lane * 64 + i] = lo;
+    }
+    __syncthreads();
+    // rows c0 .. c0 + kTaCols - 1 of W2^T are contiguous (row length nb <= 64)
+    const int ncols = min(kTaCols, ncol - c0);
+    float *dh = W2hi + ((long long)b * n + c0) * nb, *dl = W2lo + ((long long)b * n + c0) * nb;
+    if (nb == 64) {
+        float4 *dh4 = reinterpret_cast<float4 *>(dh), *dl4 = reinterpret_cast<float4 *>(dl);
+        const float4 *oh4 = reinterpret_cast<const float4 *>(oh), *ol4 = reinterpret_cast<const float4 *>(ol);
+        for (int e = threadIdx.x; e < ncols * 16; e += blockDim.x) { dh4[e] = oh4[e]; dl4[e] = ol4[e]; }
+    } else {
+        for (int e = threadIdx.x; e < ncols * nb; e += blockDim.x) {
+            const int c = e / nb, i = e - c * nb;
+            dh[e] = oh[c * 64 + i];
+            dl[e] = ol[c * 64 + i];
+        }
     }
 }
 
@@ -390,9 +411,9 @@ static int qr_apply_block(QrWS &w, int j0, int pw, int panel, int c0, int ncol, 
         PSVD_TRY(launch_gemm(nullptr, nullptr, &ah, &al, &bh, &bl, s, B, e, st));
     }
     {
-        dim3 g((ncol + 127) / 128, B);
-        qr_tapply_kernel<<<g, 128, sizeof(float) * pw * pw, st>>>(w.Wp, ks, B, nb, pw, n, ncol, w.Tm, w.npan, panel,
-                                                                 trans, w.skip, w.W2hi, w.W2lo);
+        dim3 g((ncol + kTaCols - 1) / kTaCols, B);
+        qr_tapply_kernel<<<g, 32 * kTaWarps, 0, st>>>(w.Wp, ks, B, nb, pw, n, ncol, w.Tm, w.npan, panel, trans,
+                                                      w.skip, w.W2hi, w.W2lo);
         count_launch(1);
         PSVD_TRY(cudaGetLastError());
     }
