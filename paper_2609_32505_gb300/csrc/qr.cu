@@ -141,8 +141,11 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(PanelArgs P) {
             }
         }
         __syncthreads();
-        for (int t = tid; t < CL * 2 * live; t += blockDim.x) {
-            const int peer = t / (2 * live), k = t - peer * 2 * live;
+        // the row-j values are nonzero only in the CTA that owns row j: only it sends them,
+        // and the readers take them from its slot
+        const int nsend = own ? 2 * live : live;
+        for (int t = tid; t < CL * nsend; t += blockDim.x) {
+            const int peer = t / nsend, k = t - peer * nsend;
             const int e = k < live ? c + k : nb + c + (k - live);
             float *dst = cluster.map_shared_rank(xch + ((long long)par * CL + rank) * 2 * nb, peer);
             dst[e] = vec[e];
@@ -153,8 +156,10 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(PanelArgs P) {
         if (tid < 32) {
             const int lane = tid;
             const float *slots = xch + (long long)par * CL * 2 * nb;
-            float alpha = 0.f, s2 = 0.f;
-            for (int q = 0; q < CL; ++q) { alpha += slots[q * 2 * nb + nb + c]; s2 += slots[q * 2 * nb + c]; }
+            const float *oslot = slots + (long long)((j - j0) / S) * 2 * nb;   // the owner of row j
+            float s2 = 0.f;
+            for (int q = 0; q < CL; ++q) s2 += slots[q * 2 * nb + c];
+            const float alpha = oslot[nb + c];
             const float fa = alpha, f2 = s2;
             float beta, tau, scal;
             if (f2 == 0.f) { beta = fa; tau = 0.f; scal = 0.f; }
@@ -164,9 +169,9 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(PanelArgs P) {
                 scal = 1.f / (fa - beta);
             }
             for (int k = c + 1 + lane; k < pw; k += 32) {
-                float pc = 0.f, yj = 0.f;
-                for (int q = 0; q < CL; ++q) { pc += slots[q * 2 * nb + k]; yj += slots[q * 2 * nb + nb + k]; }
-                coef[k] = tau * (yj + pc * scal);
+                float pc = 0.f;
+                for (int q = 0; q < CL; ++q) pc += slots[q * 2 * nb + k];
+                coef[k] = tau * (oslot[nb + k] + pc * scal);
             }
             if (lane == 0) {
                 scal_s[0] = scal;
