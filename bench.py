@@ -471,7 +471,43 @@ def main():
             del U, S, VT
         return {"workload": "8 x (4096 x 1024) iid N(0, 1/1024), svd_fwd", **out}
 
+    def small_report():
+        # the small configuration: one 256 x 256 matrix (singular values log-uniform in
+        # [1e-3, 1]), plain FP32 path with the classical Newton-Schulz polar iteration, full
+        # U, S, V^T; latency of svd_fwd and of svd_fwd + svd_bwd in microseconds (launch-bound
+        # at this size), and the errors against the matrix's own factors
+        a, s = W.small_square(1, 256)
+        As = torch.from_numpy(a.astype(np.float32))[None].to(dev).contiguous()
+        out = {}
+        for name, sched in (("newton_schulz", P.SCHED_NS), ("cans", P.SCHED_CANS)):
+            o = P.make_opts(precision=P.PREC_FP32, schedule=sched)
+            U, S, VT, info = P.svd_fwd(As, o, return_info=True)
+            gU, gS, gV = torch.ones_like(U), torch.ones_like(S), torch.ones_like(VT)
+            ts_f, ts_fb = [], []
+            for _ in range(25):
+                for ts, bwd in ((ts_f, False), (ts_fb, True)):
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    u, sv, vt = P.svd_fwd(As, o)
+                    if bwd:
+                        P.svd_bwd(As, u, sv, vt, gU, gS, gV, eps=EPS)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1) * 1e3)
+            ad = As[0].double()
+            rec = float(torch.linalg.matrix_norm(ad - (U[0].double() * S[0].double()) @ VT[0].double())
+                        / torch.linalg.matrix_norm(ad))
+            serr = float(np.max(np.abs(S[0].double().cpu().numpy() - np.sort(s)[::-1])) / np.max(s))
+            out[name] = {"fwd_us": float(np.median(ts_f[5:])), "fwd_bwd_us": float(np.median(ts_fb[5:])),
+                         "polar_steps": info[0]["iters"], "recon": rec, "sigma_err_rel_smax": serr}
+        return {"workload": "one 256 x 256 fp32 matrix, sigma log-uniform in [1e-3, 1], plain path", **out}
+
     reports = {}
+    try:
+        reports["small_256"] = small_report()
+    except Exception as exc:
+        reports["small_256_error"] = f"{type(exc).__name__}: {exc}"
     for key, fn in (("sweep", extra_reports), ("rectangular_preqr", rect_report)):
         try:
             r = fn()

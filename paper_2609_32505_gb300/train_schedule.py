@@ -77,7 +77,7 @@ def features_and_labels(seeds, n, device):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=DEFAULT_OUT)
-    ap.add_argument("--sizes", default="256:768,512:512,1024:256,2048:96,4096:32")
+    ap.add_argument("--sizes", default="256:6000,512:6000,1024:5000,2048:2400,4096:600")
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--quantile", type=float, default=0.95)
     ap.add_argument("--evaluate", type=int, default=0, help="evaluate the stored network on this many matrices")
