@@ -442,8 +442,10 @@ PSVD_DEV int sturm_count_ff(const float4 *__restrict__ dd, int n, ff x, float pi
     return c;
 }
 
-// dd[b][t] = {split(d_t / tn), split(e_{t-1}^2 / tn^2)} for the float-float Sturm counts.
-__global__ void sturm_prep_kernel(const double *D, const double *E, const double *tnorm, int n, float4 *dd) {
+// dd[b][t] = {split(d_t / tn), split(e_{t-1}^2 / tn^2)} for the float-float Sturm counts, and
+// de[b][t] = {split(d_t / tn), split(e_t / tn)} (e_{n-1} = 0) for float-float inverse iteration.
+__global__ void sturm_prep_kernel(const double *D, const double *E, const double *tnorm, int n, float4 *dd,
+                                  float4 *de) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
     if (t >= n) return;
     const double tn = tnorm[b], inv = tn > 0.0 ? 1.0 / tn : 0.0;
@@ -452,6 +454,9 @@ __global__ void sturm_prep_kernel(const double *D, const double *E, const double
     const double e2 = ev * ev;
     const float dh = (float)dv, eh = (float)e2;
     dd[(long long)b * n + t] = make_float4(dh, (float)(dv - (double)dh), eh, (float)(e2 - (double)eh));
+    const double en = t + 1 < n ? E[(long long)b * n + t] * inv : 0.0;
+    const float enh = (float)en;
+    de[(long long)b * n + t] = make_float4(dh, (float)(dv - (double)dh), enh, (float)(en - (double)enh));
 }
 
 // 1/a by the hardware's approximate reciprocal refined with two Newton-Raphson steps
@@ -548,8 +553,11 @@ constexpr double kClusterTol = 1e-11;
 
 struct InvitParams {
     const double *D, *E, *tn;
+    const float4 *de;        // [b][j] = {d_j / tn, e_j / tn} as float-float pairs (e_{n-1} = 0)
+    const double *lam0;      // the eigenvalues before inverse iteration (for the gaps)
     double *lam;
     double *xs, *u0, *u1, *u2, *lm;
+    float *xf;               // the normalized eigenvectors, interleaved [n][stride] like xs
     unsigned *piv;           // pivot flags, bit (j % 32) of word [j / 32][t]
     int n, first, count;     // vectors [first, first + count) of the flattened (b, i) index
     long long stride;        // = chunk
@@ -609,6 +617,7 @@ PSVD_DEV void iv_stream(double *ring, int nsteps, const IvArr (&arr)[NA], Body b
     for (int st = 0; st < nst; ++st) {
         cp_async_wait_ring();
         const double *buf = ring + (st % kIvR) * kIvStage + lane;
+#pragma unroll 4
         for (int jj = 0; jj < kIvJ; ++jj) {
             const int k = st * kIvJ + jj;
             if (k >= nsteps) break;
@@ -705,7 +714,7 @@ PSVD_DEV double iv_backward(const InvitParams &P, double *ring, int n, int t) {
     return nrm;
 }
 
-// x <- scale * x and the Rayleigh quotient x^T T x of the scaled vector.
+// xf <- scale * x (rounded to FP32) and the Rayleigh quotient x^T T x of the scaled vector.
 PSVD_DEV double iv_finish(const InvitParams &P, double *ring, const double *D, const double *E, int n, int t,
                           double scale) {
     const long long s = P.stride;
@@ -715,7 +724,7 @@ PSVD_DEV double iv_finish(const InvitParams &P, double *ring, const double *D, c
     iv_stream(ring, n, arr,
               [&](int j, const double *p) {
                   const double xj = IV_SLOT(p, 0) * scale;
-                  x[(long long)j * s + t] = xj;
+                  P.xf[(long long)j * s + t] = (float)xj;
                   r += IV_SLOT(p, 1) * xj * xj;
                   if (j > 0) r += 2.0 * IV_SLOT(p, 2) * prev * xj;
                   prev = xj;
@@ -723,24 +732,200 @@ PSVD_DEV double iv_finish(const InvitParams &P, double *ring, const double *D, c
     return r;
 }
 
+// ------------------------------------------------ inverse iteration in float-float
+// The same factorization and solves on T / tn with two-float values on the FP32 pipe, for
+// vectors whose eigenvalue is at least kIvFFGap ||T|| from its neighbours.  The factors
+// and the vectors between passes are stored as (hi, lo) pairs in the 8-byte slots of the
+// FP64 arrays.  A factorization in ~2^-46 arithmetic is exact for a matrix within a few
+// 2^-46 ||T|| of T, so these vectors are off by ~1e-13 ||T|| / gap <= 1e-7; closer
+// eigenvalues keep the FP64 recurrences above.  Rounding the right-hand sides (the stored
+// vectors) perturbs nothing but the start of each solve.
+constexpr double kIvFFGap = 1e-6;
+constexpr float kIvFFTiny = 0x1p-44f;          // pivot floor on T / tn
+
+PSVD_DEV ff ff_mul(ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const float h = __fadd_rn(p, e);
+    return ff{h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+PSVD_DEV ff ff_mulf(ff a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    const float h = __fadd_rn(p, e);
+    return ff{h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+PSVD_DEV ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
+PSVD_DEV ff ff_sel(bool c, ff a, ff b) { return ff{c ? a.hi : b.hi, c ? a.lo : b.lo}; }
+PSVD_DEV ff ff_ld(const double *slot) {
+    const float2 v = *reinterpret_cast<const float2 *>(slot);
+    return ff{v.x, v.y};
+}
+PSVD_DEV void ff_st(double *slot, ff v) { *reinterpret_cast<float2 *>(slot) = make_float2(v.hi, v.lo); }
+PSVD_DEV float iv_start_f(int i, int j) {
+    unsigned h = (unsigned)i * 0x9E3779B1u ^ ((unsigned)j + 0x7F4A7C15u) * 0x85EBCA77u;
+    h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
+    return __fmaf_rn((float)(h >> 8), 0x1p-23f, -0.9375f);          // in [-0.9375, 1.0625)
+}
+
+// Factor T/tn - mu I = P L U as iv_factor does; stored per row: u0 = 1 / pivot, u1 u0 and
+// u2 u0 (the superdiagonals pre-scaled, so that each back-substitution step is one
+// dependent multiply-add), and the multiplier.  The pivot choice and both row orders are
+// evaluated with selects (no divergence inside the warp).
+PSVD_DEV void ivf_factor(const InvitParams &P, double *ring, const float4 *de, int n, ff mu, int t) {
+    const long long s = P.stride;
+    const float4 r0 = de[0];
+    ff a = ff_add(ff{r0.x, r0.y}, ff_neg(mu));
+    ff bs = ff{r0.z, r0.w};
+    unsigned word = 0;
+    const double *dd = reinterpret_cast<const double *>(de);     // (d, e) pairs: 2 slots per row
+    const IvArr arr[3] = {{dd + 2, 2, 0, n - 1}, {dd + 1, 2, 0, n - 1}, {dd + 3, 2, 0, n - 1}};
+    iv_stream(ring, n - 1, arr,
+              [&](int j, const double *p) {
+                  const ff dn = ff_add(ff_ld(&IV_SLOT(p, 0)), ff_neg(mu));
+                  const ff c = ff_ld(&IV_SLOT(p, 1));
+                  const ff en = ff_ld(&IV_SLOT(p, 2));
+                  const bool pv = fabsf(a.hi) < fabsf(c.hi);
+                  ff den = ff_sel(pv, c, a);
+                  if (fabsf(den.hi) < kIvFFTiny) den = ff{den.hi < 0.f ? -kIvFFTiny : kIvFFTiny, 0.f};
+                  const ff m = ff_div(ff_sel(pv, a, c), den);
+                  const ff rp = ff_div(ff{1.f, 0.f}, den);
+                  const ff y = ff_sel(pv, dn, bs);
+                  a = ff_add(ff_sel(pv, bs, dn), ff_neg(ff_mul(m, y)));
+                  const ff me = ff_mul(m, en);
+                  const ff u2 = pv ? en : ff{0.f, 0.f};
+                  bs = ff_sel(pv, ff_neg(me), en);
+                  const long long o = (long long)j * s + t;
+                  ff_st(P.u0 + o, rp);
+                  ff_st(P.u1 + o, ff_mul(y, rp));
+                  ff_st(P.u2 + o, ff_mul(u2, rp));
+                  ff_st(P.lm + o, m);
+                  word |= (unsigned)pv << (j & 31);
+                  if ((j & 31) == 31 || j == n - 2) { P.piv[(long long)(j >> 5) * s + t] = word; word = 0; }
+              });
+    if (fabsf(a.hi) < kIvFFTiny) a = ff{a.hi < 0.f ? -kIvFFTiny : kIvFFTiny, 0.f};
+    ff_st(P.u0 + (long long)(n - 1) * s + t, ff_div(ff{1.f, 0.f}, a));
+}
+
+// Forward part of one solve (the pivots and L), right-hand side scale * x or the start vector.
+PSVD_DEV void ivf_forward(const InvitParams &P, double *ring, int n, int t, int i, bool first, float scale) {
+    const long long s = P.stride;
+    double *x = P.xs;
+    ff carry = first ? ff{iv_start_f(i, 0), 0.f} : ff_mulf(ff_ld(x + t), scale);
+    unsigned pword = 0;
+    unsigned pnext = P.piv[t];
+    const IvArr arr[2] = {{x + s + t, s, 0, first ? 0 : n - 1}, {P.lm + t, s, 0, n - 1}};
+    iv_stream(ring, n - 1, arr,
+              [&](int j, const double *p) {
+                  if ((j & 31) == 0) {
+                      pword = pnext;
+                      const long long nw = (long long)((j >> 5) + 1);
+                      if ((nw << 5) < n - 1) pnext = P.piv[nw * s + t];
+                  }
+                  const ff bn = first ? ff{iv_start_f(i, j + 1), 0.f} : ff_mulf(ff_ld(&IV_SLOT(p, 0)), scale);
+                  const bool sw = (pword >> (j & 31)) & 1u;
+                  const ff a = ff_sel(sw, bn, carry);
+                  const ff b = ff_sel(sw, carry, bn);
+                  ff_st(x + (long long)j * s + t, a);
+                  carry = ff_add(b, ff_neg(ff_mul(ff_ld(&IV_SLOT(p, 1)), a)));
+              });
+    ff_st(x + (long long)(n - 1) * s + t, carry);
+}
+
+// Backward part: U x = y in place; returns ||x||^2 (float-float).
+PSVD_DEV ff ivf_backward(const InvitParams &P, double *ring, int n, int t) {
+    const long long s = P.stride;
+    double *x = P.xs;
+    const long long last = (long long)(n - 1) * s + t;
+    ff x1 = ff_mul(ff_ld(x + last), ff_ld(P.u0 + last)), x2 = ff{0.f, 0.f};
+    ff_st(x + last, x1);
+    ff nrm = ff_fma(ff_zero(), x1.hi, x1.hi);
+    const long long o0 = (long long)(n - 2) * s + t;     // row n - 2 - k at step k
+    const IvArr arr[4] = {{x + o0, -s, 0, n - 1}, {P.u0 + o0, -s, 0, n - 1}, {P.u1 + o0, -s, 0, n - 1},
+                          {P.u2 + o0, -s, 0, n - 1}};
+    iv_stream(ring, n - 1, arr,
+              [&](int k, const double *p) {
+                  ff r = ff_mul(ff_ld(&IV_SLOT(p, 0)), ff_ld(&IV_SLOT(p, 1)));
+                  r = ff_add(r, ff_neg(ff_mul(ff_ld(&IV_SLOT(p, 3)), x2)));
+                  const ff v = ff_add(r, ff_neg(ff_mul(ff_ld(&IV_SLOT(p, 2)), x1)));
+                  ff_st(x + (long long)(n - 2 - k) * s + t, v);
+                  x2 = x1;
+                  x1 = v;
+                  nrm = ff_fma(nrm, v.hi, v.hi);
+              });
+    return nrm;
+}
+
+// xf <- scale * x (FP32) and the Rayleigh quotient x^T (T/tn) x / x^T x of that vector.
+PSVD_DEV double ivf_finish(const InvitParams &P, double *ring, const float4 *de, int n, int t, float scale) {
+    const long long s = P.stride;
+    const double *x = P.xs;
+    const double *dd = reinterpret_cast<const double *>(de);
+    ff num = ff_zero(), den = ff_zero();
+    float prev = 0.f;
+    const IvArr arr[3] = {{x + t, s, 0, n}, {dd, 2, 0, n}, {dd - 1, 2, 1, n}};   // e_{j-1} from j = 1 on
+    iv_stream(ring, n, arr,
+              [&](int j, const double *p) {
+                  const float xj = __fmul_rn(__fadd_rn(ff_ld(&IV_SLOT(p, 0)).hi, ff_ld(&IV_SLOT(p, 0)).lo), scale);
+                  P.xf[(long long)j * s + t] = xj;
+                  // x_j (d_j x_j + 2 e_{j-1} x_{j-1})
+                  ff q = ff_mulf(ff_ld(&IV_SLOT(p, 1)), xj);
+                  if (j > 0) q = ff_add(q, ff_mulf(ff_ld(&IV_SLOT(p, 2)), __fmul_rn(2.f, prev)));
+                  num = ff_add(num, ff_mulf(q, xj));
+                  den = ff_fma(den, xj, xj);
+                  prev = xj;
+              });
+    return ((double)num.hi + (double)num.lo) / ((double)den.hi + (double)den.lo);
+}
+
 // One warp per block: 32 eigenvectors, each by inverse iteration from a fixed
 // pseudo-random start.  The bisection shift is accurate to ~1e-7 ||T||: three solves
-// reduce the other components by (shift error / gap)^3.
+// reduce the other components by (shift error / gap)^3.  A warp whose 32 eigenvalues are
+// all at least kIvFFGap ||T|| from their neighbours runs the float-float recurrences, the
+// others the FP64 ones (the choice is per warp, so no warp runs both).
 __global__ void __launch_bounds__(kIvW) tri_invit_kernel(InvitParams P) {
     extern __shared__ __align__(16) double ivring[];
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= P.count) return;
     const int n = P.n;
     const long long gi = (long long)P.first + t;
     const int b = (int)(gi / n), i = (int)(gi % n);
-    const double *D = P.D + (long long)b * n, *E = P.E + (long long)b * n;
-    const double tn = P.tn[b];
-    const double mu = P.lam[gi];
+    bool ffok = true;
+    double tn = 0.0;
+    if (t < P.count) {
+        tn = P.tn[b];
+        const double *lb = P.lam0 + (long long)b * n;
+        double g = 1e300;
+        if (i > 0) g = fmin(g, lb[i - 1] - lb[i]);
+        if (i + 1 < n) g = fmin(g, lb[i] - lb[i + 1]);
+        ffok = n > 1 && tn > 0.0 && g >= kIvFFGap * tn;
+    }
+    const bool use_ff = __all_sync(0xffffffffu, ffok);
+    if (t >= P.count) return;
     const long long s = P.stride;
-    if (n == 1) { P.xs[t] = 1.0; return; }
+    const double mu = P.lam[gi];
+    if (use_ff) {
+        const float4 *de = P.de + (long long)b * n;
+        const double ms = mu / tn;
+        const float mh = (float)ms;
+        ivf_factor(P, ivring, de, n, ff{mh, (float)(ms - (double)mh)}, t);
+        float scale = 1.f;
+        for (int it = 0; it < 3; ++it) {
+            ivf_forward(P, ivring, n, t, i, it == 0, scale);
+            const ff nrm = ivf_backward(P, ivring, n, t);
+            const double nv = (double)nrm.hi + (double)nrm.lo;
+            scale = nv > 0.0 ? (float)(1.0 / sqrt(nv)) : 0.f;
+        }
+        P.lam[gi] = ivf_finish(P, ivring, de, n, t, scale) * tn;
+        return;
+    }
+    const double *D = P.D + (long long)b * n, *E = P.E + (long long)b * n;
+    if (n == 1) { P.xf[t] = 1.f; return; }
     if (!(tn > 0.0)) {
         // T = 0: every vector is an eigenvector; take the unit vectors
-        for (int j = 0; j < n; ++j) P.xs[j * s + t] = j == i ? 1.0 : 0.0;
+        for (int j = 0; j < n; ++j) P.xf[j * s + t] = j == i ? 1.f : 0.f;
         P.lam[gi] = 0.0;
         return;
     }
@@ -800,25 +985,28 @@ __global__ void tri_cluster_kernel(InvitParams P, const double *bisect_lam, doub
         if (i1 - i0 >= 2) {
             for (int i = i0; i < i1; ++i) {
                 const int ti = base + i;
+                float *xf = P.xf;
                 for (int l = i0; l < i; ++l) {
                     const int tl = base + l;
                     double dot = 0.0;
-                    for (int j = threadIdx.x; j < n; j += blockDim.x) dot += P.xs[j * s + ti] * P.xs[j * s + tl];
+                    for (int j = threadIdx.x; j < n; j += blockDim.x)
+                        dot += (double)xf[j * s + ti] * (double)xf[j * s + tl];
                     dot = block_sum(dot, red);
-                    for (int j = threadIdx.x; j < n; j += blockDim.x) P.xs[j * s + ti] -= dot * P.xs[j * s + tl];
+                    for (int j = threadIdx.x; j < n; j += blockDim.x)
+                        xf[j * s + ti] = (float)((double)xf[j * s + ti] - dot * (double)xf[j * s + tl]);
                     __syncthreads();
                 }
                 double nr = 0.0;
-                for (int j = threadIdx.x; j < n; j += blockDim.x) nr += P.xs[j * s + ti] * P.xs[j * s + ti];
+                for (int j = threadIdx.x; j < n; j += blockDim.x) nr += (double)xf[j * s + ti] * (double)xf[j * s + ti];
                 nr = block_sum(nr, red);
                 const double inv = nr > 0 ? 1.0 / sqrt(nr) : 0.0;
-                for (int j = threadIdx.x; j < n; j += blockDim.x) P.xs[j * s + ti] *= inv;
+                for (int j = threadIdx.x; j < n; j += blockDim.x) xf[j * s + ti] = (float)((double)xf[j * s + ti] * inv);
                 __syncthreads();
                 double r = 0.0;
                 for (int j = threadIdx.x; j < n; j += blockDim.x) {
-                    const double xj = P.xs[j * s + ti];
+                    const double xj = xf[j * s + ti];
                     r += D[j] * xj * xj;
-                    if (j + 1 < n) r += 2.0 * E[j] * xj * P.xs[(j + 1) * s + ti];
+                    if (j + 1 < n) r += 2.0 * E[j] * xj * (double)xf[(j + 1) * s + ti];
                 }
                 r = block_sum(r, red);
                 if (threadIdx.x == 0) P.lam[(long long)b * n + i] = r;
@@ -850,24 +1038,24 @@ __global__ void tri_cluster_kernel(InvitParams P, const double *bisect_lam, doub
     }
 }
 
-// Z^T rows (eigenvectors of T) from the interleaved FP64 vectors -> V^T split (n x ldn)
-__global__ void zt_store_kernel(const double *xs, long long stride, int n, int first_b, int first, float *VThi,
+// Z^T rows (eigenvectors of T) from the interleaved FP32 vectors -> V^T split (n x ldn)
+__global__ void zt_store_kernel(const float *xs, long long stride, int n, int first_b, int first, float *VThi,
                                 float *VTlo, long long ldn) {
-    __shared__ double tile[32][33];
+    __shared__ float tile[32][33];
     const int bb = blockIdx.z;
     const int b = first_b + bb;
     const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;   // i: eigen index, j: component
     const long long tb = (long long)b * n - first;
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int j = j0 + r, i = i0 + threadIdx.x;
-        tile[r][threadIdx.x] = (j < n && i < n) ? xs[(long long)j * stride + tb + i] : 0.0;
+        tile[r][threadIdx.x] = (j < n && i < n) ? xs[(long long)j * stride + tb + i] : 0.f;
     }
     __syncthreads();
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int i = i0 + r, j = j0 + threadIdx.x;
         if (i < n && j < n) {
             float h, l;
-            split_tf32((float)tile[threadIdx.x][r], h, l);
+            split_tf32(tile[threadIdx.x][r], h, l);
             const long long o = (long long)b * n * ldn + (long long)i * ldn + j;
             VThi[o] = h;
             VTlo[o] = l;
@@ -877,36 +1065,69 @@ __global__ void zt_store_kernel(const double *xs, long long stride, int n, int f
 
 // ------------------------------------------------------------ back-transform
 // Upper-triangular T of the forward compact-WY form H_k0 ... H_k1-1 = I - Y T Y^T, one
-// block per (WY block, matrix), from G = Y^T Y (computed on the tensor cores, symmetric):
-// T[c][c] = tau_c,  T[:c, c] = -tau_c T[:c, :c] G[:c, c].
-__global__ void larft_kernel(const float *Gm, const float *tau, int n, int nblk, float *Tm) {
+// block per (WY block, matrix), from G = Y^T Y (computed on the tensor cores, symmetric).
+// Splitting the block's reflectors into halves a, b gives T = [T_aa, -T_aa G_ab T_bb; 0, T_bb],
+// so T is built by recursive halving: the four 32 x 32 diagonal blocks column by column
+// (T[i][c] = -tau_c sum_{i <= k < c} T[i][k] G[k][c], one warp per block, lane i holding row
+// i in registers), then the off-diagonal blocks of the 64- and 128-wide levels as two small
+// products each.  The serial depth is 32 columns instead of 128.
+static_assert(kWY % 32 == 0 && (kWY & (kWY - 1)) == 0 && kWY / 32 <= 8, "larft halving assumes 32 x 2^j reflectors");
+constexpr int kLtLd = kWY + 1;                  // padded row stride of G and T in shared memory
+constexpr size_t kLtSmem = sizeof(float) * ((size_t)2 * kWY * kLtLd + (kWY / 2) * (kWY / 2) + kWY);
+__global__ void __launch_bounds__(256) larft_kernel(const float *Gm, const float *tau, int n, int nblk, float *Tm) {
     extern __shared__ float sm2[];
-    float *G = sm2, *T = sm2 + kWY * kWY;
+    float *G = sm2, *T = G + kWY * kLtLd, *W = T + kWY * kLtLd, *ts = W + (kWY / 2) * (kWY / 2);
     const int blk = blockIdx.x, b = blockIdx.y;
     const int k0 = blk * kWY;
     const int nb = min(kWY, n - 2 - k0);
     const float *Gb = Gm + ((long long)b * nblk + blk) * kWY * kWY;
-    for (int p = threadIdx.x; p < kWY * kWY; p += blockDim.x) { G[p] = Gb[p]; T[p] = 0.f; }
+    for (int p = threadIdx.x; p < kWY * kWY; p += blockDim.x) {
+        const int r = p / kWY, c = p % kWY;
+        G[r * kLtLd + c] = Gb[p];
+        T[r * kLtLd + c] = 0.f;
+    }
+    for (int c = threadIdx.x; c < kWY; c += blockDim.x) ts[c] = c < nb ? tau[(long long)b * n + k0 + c] : 0.f;
     __syncthreads();
-    const float *tb = tau + (long long)b * n + k0;
-    if (threadIdx.x == 0) T[0] = tb[0];
-    __syncthreads();
-    // column c: entry a (< c) is a dot product over l in [a, c), one warp per entry with its
-    // lanes splitting l; G is symmetric, so its column c is read as row c (contiguous)
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int c = 1; c < nb; ++c) {
-        const float tc = tb[c];
-        for (int a = warp; a < c; a += nw) {
-            float v = 0.f;
-            for (int l = a + lane; l < c; l += 32) v += T[a * kWY + l] * G[c * kWY + l];
-            v = warp_sum(v);
-            if (lane == 0) T[a * kWY + c] = -tc * v;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < kWY / 32) {
+        const int o = 32 * warp, i = lane;
+        float tr[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < c; ++k)
+                if (k >= i) s = fmaf(tr[k], G[(o + k) * kLtLd + o + c], s);
+            tr[c] = c < i ? 0.f : (c == i ? ts[o + c] : -ts[o + c] * s);
         }
-        if (threadIdx.x == 0) T[c * kWY + c] = tc;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) T[(o + i) * kLtLd + o + c] = tr[c];
+    }
+    __syncthreads();
+    for (int h = 32; h < kWY; h *= 2) {
+        const int np = kWY / (2 * h), hh = h * h;
+        // W_p = G[a:a+h, b:b+h] T[b:b+h, b:b+h]   (a = 2 h p, b = a + h; T_bb upper triangular)
+        for (int e = threadIdx.x; e < np * hh; e += blockDim.x) {
+            const int p = e / hh, r = (e / h) % h, j = e % h;
+            const int a = 2 * h * p, bb = a + h;
+            float s = 0.f;
+            for (int k = 0; k <= j; ++k) s = fmaf(G[(a + r) * kLtLd + bb + k], T[(bb + k) * kLtLd + bb + j], s);
+            W[e] = s;
+        }
+        __syncthreads();
+        // T[a:a+h, b:b+h] = -T[a:a+h, a:a+h] W_p   (T_aa upper triangular)
+        for (int e = threadIdx.x; e < np * hh; e += blockDim.x) {
+            const int p = e / hh, r = (e / h) % h, j = e % h;
+            const int a = 2 * h * p, bb = a + h;
+            const float *wp = W + p * hh;
+            float s = 0.f;
+            for (int k = r; k < h; ++k) s = fmaf(T[(a + r) * kLtLd + a + k], wp[k * h + j], s);
+            T[(a + r) * kLtLd + bb + j] = -s;
+        }
         __syncthreads();
     }
     float *out = Tm + ((long long)b * nblk + blk) * kWY * kWY;
-    for (int p = threadIdx.x; p < kWY * kWY; p += blockDim.x) out[p] = T[p];
+    for (int p = threadIdx.x; p < kWY * kWY; p += blockDim.x) out[p] = T[(p / kWY) * kLtLd + p % kWY];
 }
 
 // S2 = S T^T (n x nb), split into TF32 hi/lo; S is the sum of `ks` K-split slices of
@@ -1189,8 +1410,8 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
         count_launch(1);
     }
     {
-        float4 *dd = reinterpret_cast<float4 *>(w.S2lo);   // B x n float4 (S2 is free until stage 4)
-        sturm_prep_kernel<<<dim3((n + 255) / 256, B), 256, 0, st>>>(w.d, w.e, tn, n, dd);
+        float4 *dd = reinterpret_cast<float4 *>(w.S2lo);   // 2 x B x n float4 (S2 is free until stage 4)
+        sturm_prep_kernel<<<dim3((n + 255) / 256, B), 256, 0, st>>>(w.d, w.e, tn, n, dd, dd + (size_t)B * n);
         dim3 g((n + 31) / 32, B);       // 32 eigenvalues x 8 lanes per block
         tri_refine_kernel<<<g, 256, 0, st>>>(dd, n, tn, kRefineNear, w.lam);
         PSVD_TRY(cudaGetLastError());
@@ -1205,13 +1426,14 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
     for (int b0 = 0; b0 < B; b0 += per) {
         const int nb = std::min(per, B - b0);
         InvitParams P;
-        P.D = w.d; P.E = w.e; P.tn = tn; P.lam = w.lam;
-        P.xs = w.xs; P.u0 = w.u0; P.u1 = w.u1; P.u2 = w.u2; P.lm = w.lm; P.piv = w.piv;
+        P.D = w.d; P.E = w.e; P.tn = tn; P.lam = w.lam; P.lam0 = bis;
+        P.de = reinterpret_cast<const float4 *>(w.S2lo) + (size_t)B * n;
+        P.xs = w.xs; P.xf = w.xf; P.u0 = w.u0; P.u1 = w.u1; P.u2 = w.u2; P.lm = w.lm; P.piv = w.piv;
         P.n = n; P.first = b0 * n; P.count = nb * n; P.stride = w.chunk;
         tri_invit_kernel<<<(P.count + kIvW - 1) / kIvW, kIvW, kIvSmem, st>>>(P);
         tri_cluster_kernel<<<nb, 256, 0, st>>>(P, bis, kClusterTol);
         dim3 g((n + 31) / 32, (n + 31) / 32, nb), blk(32, 8);
-        zt_store_kernel<<<g, blk, 0, st>>>(w.xs, w.chunk, n, b0, b0 * n, w.VThi, w.VTlo, ldn);
+        zt_store_kernel<<<g, blk, 0, st>>>(w.xf, w.chunk, n, b0, b0 * n, w.VThi, w.VTlo, ldn);
         PSVD_TRY(cudaGetLastError());
         count_launch(3);
     }
@@ -1233,9 +1455,8 @@ int eigh_forward(const float *Hs, float *S, float *VT, EighWS &w, cudaStream_t s
             EpiStore e = epi_store_plain(w.Gm + (long long)b * w.nblk * kWY * kWY, kWY, (long long)kWY * kWY, kWY, kWY);
             PSVD_TRY(launch_gemm(nullptr, nullptr, &vh, &vl, &vh, &vl, s, w.nblk, e, st));
         }
-        const size_t smem = sizeof(float) * 2 * kWY * kWY;
-        PSVD_TRY(cudaFuncSetAttribute(larft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        larft_kernel<<<dim3(w.nblk, B), 256, smem, st>>>(w.Gm, w.tau, n, w.nblk, w.Tm);
+        PSVD_TRY(cudaFuncSetAttribute(larft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLtSmem));
+        larft_kernel<<<dim3(w.nblk, B), 256, kLtSmem, st>>>(w.Gm, w.tau, n, w.nblk, w.Tm);
         PSVD_TRY(cudaFuncSetAttribute(s_times_tt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStSmem));
         PSVD_TRY(cudaGetLastError());
         count_launch(1);

@@ -27,6 +27,7 @@ struct EighWS {
     float *Gm = nullptr;                       // [B][nblk][kWY][kWY]  Y^T Y per block
     float *Gab = nullptr;                      // [B][nblk/2][kWY][kWY]  Y_a^T Y_b per pair of blocks
     double *xs = nullptr;                      // inverse-iteration vectors, interleaved [n][chunk]
+    float *xf = nullptr;                       // the normalized eigenvectors of T, interleaved [n][chunk]
     double *u0 = nullptr, *u1 = nullptr, *u2 = nullptr, *lm = nullptr;
     unsigned *piv = nullptr;            // pivot bits, [ceil(n/32)][chunk]
     unsigned *err = nullptr;
@@ -62,6 +63,7 @@ struct EighWS {
         Gm = cv.template take<float>(B64 * (nblk > 0 ? nblk : 1) * kWY * kWY);
         Gab = cv.template take<float>(B64 * (nblk > 1 ? nblk / 2 : 1) * kWY * kWY);
         xs = cv.template take<double>((long long)n * chunk);
+        xf = cv.template take<float>((long long)n * chunk);
         u0 = cv.template take<double>((long long)n * chunk);
         u1 = cv.template take<double>((long long)n * chunk);
         u2 = cv.template take<double>((long long)n * chunk);

@@ -289,13 +289,13 @@ struct EpiGram {
     __nv_bfloat16 *P16;
     float *Phi, *Plo;
     long long ldp;
-    struct Acc { double r; int p; float c1, c3; };
+    struct Acc { ff r; int p; float c1, c3; };     // ||G - I||^2 partial, float-float (FP32 pipe)
     static constexpr bool kElem = true, kTrans = true, kTail = true;
     PSVD_DEV bool staged() const { return true; }
     PSVD_DEV void tail() const {
         for (int b = threadIdx.x; b < dec.B; b += blockDim.x) decide_matrix(dec, b);
     }
-    PSVD_DEV void begin(Acc &a) const { a.r = 0.0; a.p = -1; }
+    PSVD_DEV void begin(Acc &a) const { a.r = ff_zero(); a.p = -1; }
     PSVD_DEV void load(Acc &a, int b) const {
         if (a.p < 0) { a.p = prec[b]; a.c1 = coef[2 * b]; a.c3 = coef[2 * b + 1]; }
     }
@@ -303,7 +303,7 @@ struct EpiGram {
         if (r >= n || c >= n || c < r) return;
         load(a, b);
         const float d = g - (r == c ? 1.f : 0.f);
-        a.r += (r == c ? 1.0 : 2.0) * (double)d * d;
+        a.r = ff_fma(a.r, r == c ? d : 2.f * d, d);
         const float pv = a.c3 * g + (r == c ? a.c1 : 0.f);
         store_prec(a.p, (long long)b * n * ldp + (long long)r * ldp + c, pv, P16, Phi, Plo);
     }
@@ -325,7 +325,7 @@ struct EpiGram {
         trans(a, b, r, c0, v);
     }
     PSVD_DEV void finish(Acc &a, int b, int, int) const {
-        const double s = warp_sum(a.r);
+        const double s = warp_sum((double)a.r.hi + (double)a.r.lo);
         if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(&res[b], s);
     }
 };
