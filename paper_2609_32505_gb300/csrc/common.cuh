@@ -273,6 +273,23 @@ PSVD_DEV ff ff_fma(ff a, float x, float y) {
     const float h = __fadd_rn(s, t);
     return ff{h, __fsub_rn(t, __fsub_rn(h, s))};
 }
+// a * b and a * (float) b: the exact product of the leading words plus the cross terms
+PSVD_DEV ff ff_mul(ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const float h = __fadd_rn(p, e);
+    return ff{h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+PSVD_DEV ff ff_mulf(ff a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    const float h = __fadd_rn(p, e);
+    return ff{h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+PSVD_DEV ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
 PSVD_DEV ff warp_sum(ff v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

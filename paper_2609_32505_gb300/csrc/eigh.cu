@@ -743,22 +743,6 @@ PSVD_DEV double iv_finish(const InvitParams &P, double *ring, const double *D, c
 constexpr double kIvFFGap = 1e-6;
 constexpr float kIvFFTiny = 0x1p-44f;          // pivot floor on T / tn
 
-PSVD_DEV ff ff_mul(ff a, ff b) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
-    e = __fmaf_rn(a.lo, b.hi, e);
-    const float h = __fadd_rn(p, e);
-    return ff{h, __fsub_rn(e, __fsub_rn(h, p))};
-}
-PSVD_DEV ff ff_mulf(ff a, float b) {
-    const float p = __fmul_rn(a.hi, b);
-    float e = __fmaf_rn(a.hi, b, -p);
-    e = __fmaf_rn(a.lo, b, e);
-    const float h = __fadd_rn(p, e);
-    return ff{h, __fsub_rn(e, __fsub_rn(h, p))};
-}
-PSVD_DEV ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
 PSVD_DEV ff ff_sel(bool c, ff a, ff b) { return ff{c ? a.hi : b.hi, c ? a.lo : b.lo}; }
 PSVD_DEV ff ff_ld(const double *slot) {
     const float2 v = *reinterpret_cast<const float2 *>(slot);
