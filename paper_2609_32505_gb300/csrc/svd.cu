@@ -156,17 +156,54 @@ __global__ void qr_form_q_kernel(QrParams P, float *qbuf) {
 }
 
 // ------------------------------------------------------------ mixed-precision correction
-__global__ void skewT_kernel(const float *Hraw, int n, float *hi, float *lo, long long ld) {
-    // K^T = -skew(Hraw) stored as the B operand of V^T K (B[j][k] = K[k][j])
+__global__ void skewT_kernel(const float *Hraw, int n, float *hi, float *lo, long long ld, unsigned *kmax) {
+    // K^T = -skew(Hraw) stored as the B operand of V^T K (B[j][k] = K[k][j]); the largest
+    // |K_ij| of each matrix goes to kmax (float bits, one atomic per block)
+    __shared__ unsigned wmax[8];
     const int b = blockIdx.z;
     const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
-    if (i >= n || j >= n) return;
-    const float *h = Hraw + (long long)b * n * n;
-    const float kt = 0.5f * (h[(long long)j * n + i] - h[(long long)i * n + j]);
-    float hh, ll;
-    split_tf32(kt, hh, ll);
-    hi[(long long)b * n * ld + (long long)i * ld + j] = hh;
-    lo[(long long)b * n * ld + (long long)i * ld + j] = ll;
+    unsigned bits = 0;
+    if (i < n && j < n) {
+        const float *h = Hraw + (long long)b * n * n;
+        const float kt = 0.5f * (h[(long long)j * n + i] - h[(long long)i * n + j]);
+        float hh, ll;
+        split_tf32(kt, hh, ll);
+        hi[(long long)b * n * ld + (long long)i * ld + j] = hh;
+        lo[(long long)b * n * ld + (long long)i * ld + j] = ll;
+        bits = __float_as_uint(fabsf(kt));
+    }
+    const int t = threadIdx.y * 16 + threadIdx.x;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, o));
+    if ((t & 31) == 0) wmax[t >> 5] = bits;
+    __syncthreads();
+    if (t == 0) {
+        unsigned m = wmax[0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) m = max(m, wmax[w]);
+        if (m) atomicMax(&kmax[b], m);
+    }
+}
+
+// Precision of the correction's products, per matrix.  TF32 rounds each operand to 2^-11
+// relative, so a product whose result is a small correction can drop the split when its
+// absolute error stays below FP32 resolution:
+//  which = 0 (V^T K and (V^T K) V, then X = Ktilde / (s_i + s_j)): TF32 when
+//    2^-11 max|K| / (2 s_min) <= 2^-21, the bound of the error this puts into X;
+//  which = 1 (X V^T, added to V^T): TF32 when 2^-11 max|X| <= 2^-23.
+// Otherwise (or for a non-finite bound) the split-TF32 products are kept.
+__global__ void corr_prec_kernel(const unsigned *vmax, const float *S, int n, int B, int which, int *prec) {
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        const float v = __uint_as_float(vmax[b]);
+        bool tf32;
+        if (which == 0) {
+            const float smin = S[(long long)b * n + n - 1];
+            tf32 = smin > 0.f && v * 0x1p-11f <= 0x1p-21f * 2.f * smin;
+        } else {
+            tf32 = v * 0x1p-11f <= 0x1p-23f;
+        }
+        prec[b] = tf32 ? PREC_TF32 : PREC_TF32X3;
+    }
 }
 
 // X = Ktilde / (s_i + s_j) (skew); writes X split into TF32 hi/lo (the first-order
@@ -436,7 +473,8 @@ struct SvdWS {
     float *Vhi = nullptr, *Vlo = nullptr;            // V = (V^T)^T split
     float *Khi = nullptr, *Klo = nullptr, *T1 = nullptr, *T1hi = nullptr, *T1lo = nullptr, *Kt = nullptr;
     float *X = nullptr, *Xneg = nullptr, *X2 = nullptr, *F = nullptr, *Ft = nullptr, *VEt = nullptr;
-    unsigned *xmax = nullptr;
+    unsigned *xmax = nullptr, *kmax = nullptr;
+    int *cprec = nullptr;        // [2][B] precision of the correction products (corr_prec_kernel)
     int *mflag = nullptr;
     double *rsums = nullptr;     // [B][2] reconstruction-check sums
     float *Yp = nullptr;         // [B][kProbes][n] sigma (V^T z) for the check
@@ -481,6 +519,8 @@ struct SvdWS {
             Ft = cv.template take<float>(B64 * nn);
             VEt = cv.template take<float>(B64 * nn * 2);
             xmax = cv.template take<unsigned>(B64);
+            kmax = cv.template take<unsigned>(B64);
+            cprec = cv.template take<int>(B64 * 2);
             rsums = cv.template take<double>(B64 * 2);
             Yp = cv.template take<float>(B64 * kProbes * n);
         }
@@ -508,6 +548,20 @@ static int gemm3(const float *ahi, const float *alo, int M, int K, long long lda
     return r == cudaSuccess ? PSVD_OK : PSVD_ERR_CUDA;
 }
 
+// As gemm3, with the precision of each matrix read on the device from prec[B] (TF32 or
+// split-TF32; both operand splits supplied).
+template <class Epi>
+static int gemm3p(const float *ahi, const float *alo, int M, int K, long long lda, long long bsa, const float *bhi,
+                  const float *blo, int N, long long ldb, long long bsb, int B, const int *prec, const Epi &e,
+                  unsigned *err, cudaStream_t st) {
+    MatView vah = view_of(ahi, M, K, lda, bsa, B), val = view_of(alo, M, K, lda, bsa, B);
+    MatView vbh = view_of(bhi, N, K, ldb, bsb, B), vbl = view_of(blo, N, K, ldb, bsb, B);
+    GemmShape s;
+    memset(&s, 0, sizeof(s));
+    s.M = M; s.N = N; s.K = K; s.prec_uniform = PREC_TF32X3; s.prec = prec; s.err = err;
+    return launch_gemm(nullptr, nullptr, &vah, &val, &vbh, &vbl, s, B, e, st) == cudaSuccess ? PSVD_OK : PSVD_ERR_CUDA;
+}
+
 int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, const psvd_opts &o, psvd_info *info,
                 cudaStream_t st) {
     PolarWS &p = w.pw;
@@ -526,22 +580,25 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
         SplitOut vo;
         vo.hi = w.Vhi; vo.lo = w.Vlo; vo.ld = ld; vo.bstride = nn;
         if (prepare_operand(vthi, ld, nn, B, n, n, true, 1.f, nullptr, vo, st)) return PSVD_ERR_CUDA;
-        skewT_kernel<<<g16, b16, 0, st>>>(p.Hraw, n, w.Khi, w.Klo, ld);     // K^T, K = skew(Hhat)
-        count_launch(1);
+        if (cudaMemsetAsync(w.kmax, 0, sizeof(unsigned) * (size_t)B, st)) return PSVD_ERR_CUDA;
+        skewT_kernel<<<g16, b16, 0, st>>>(p.Hraw, n, w.Khi, w.Klo, ld, w.kmax);     // K^T, K = skew(Hhat)
+        corr_prec_kernel<<<1, 32, 0, st>>>(w.kmax, w.S, n, B, 0, w.cprec);
+        count_launch(2);
         // T1 = V^T K   (B operand B[j][k] = K[k][j] = K^T[j][k])
         EpiStore e1 = epi_store_plain(w.T1, n, (long long)n * n, n, n);
-        if (int rc = gemm3(vthi, vtlo, n, n, ld, nn, w.Khi, w.Klo, n, ld, nn, B, PREC_TF32X3, e1, p.err, st)) return rc;
+        if (int rc = gemm3p(vthi, vtlo, n, n, ld, nn, w.Khi, w.Klo, n, ld, nn, B, w.cprec, e1, p.err, st)) return rc;
         SplitOut to;
         to.hi = w.T1hi; to.lo = w.T1lo; to.ld = ld; to.bstride = nn;
         if (prepare_operand(w.T1, n, (long long)n * n, B, n, n, false, 1.f, nullptr, to, st)) return PSVD_ERR_CUDA;
         // Ktilde = T1 V   (B operand B[j][k] = V[k][j] = V^T[j][k])
         EpiStore e2 = epi_store_plain(w.Kt, n, (long long)n * n, n, n);
-        if (int rc = gemm3(w.T1hi, w.T1lo, n, n, ld, nn, vthi, vtlo, n, ld, nn, B, PREC_TF32X3, e2, p.err, st)) return rc;
+        if (int rc = gemm3p(w.T1hi, w.T1lo, n, n, ld, nn, vthi, vtlo, n, ld, nn, B, w.cprec, e2, p.err, st)) return rc;
         if (cudaMemsetAsync(w.xmax, 0, sizeof(unsigned) * (size_t)B, st)) return PSVD_ERR_CUDA;
         corr_x_kernel<<<dim3((n + 31) / 32, (n + 31) / 32, B), dim3(32, 8), 0, st>>>(w.Kt, w.S, n, w.X, w.Ft, w.Xneg,
                                                                                     ld, w.xmax);   // X_lo in Ft
         sigma_refresh_kernel<<<dim3((n + 7) / 8, B), 256, 0, st>>>(w.X, w.S, n, ld, Sout, nullptr);
-        count_launch(2);
+        corr_prec_kernel<<<1, 32, 0, st>>>(w.xmax, w.S, n, B, 1, w.cprec + B);
+        count_launch(3);
         // X^2 = X X   (B operand B[j][k] = X[k][j] = -X[j][k])
         EpiStore e3 = epi_store_plain(w.X2, n, (long long)n * n, n, n);
         if (int rc = gemm3(w.X, nullptr, n, n, ld, nn, w.Xneg, nullptr, n, ld, nn, B, PREC_TF32, e3, p.err, st)) return rc;
@@ -555,7 +612,7 @@ int svd_forward(const float *A, float *U, float *Sout, float *VT, SvdWS &w, cons
         // X V^T (split-TF32, into T1) and h V^T (TF32, into Kt); B operand B[j][k] = V^T[k][j] = V[j][k]
         float *VEt_hi = w.VEt, *VEt_lo = w.VEt + (long long)B * nn;
         EpiStore e4 = epi_store_plain(w.T1, n, (long long)n * n, n, n);
-        if (int rc = gemm3(w.X, w.Ft, n, n, ld, nn, w.Vhi, w.Vlo, n, ld, nn, B, PREC_TF32X3, e4, p.err, st)) return rc;
+        if (int rc = gemm3p(w.X, w.Ft, n, n, ld, nn, w.Vhi, w.Vlo, n, ld, nn, B, w.cprec + B, e4, p.err, st)) return rc;
         EpiStore e5 = epi_store_plain(w.Kt, n, (long long)n * n, n, n);
         if (int rc = gemm3(w.F, nullptr, n, n, ld, nn, w.Vhi, nullptr, n, ld, nn, B, PREC_TF32, e5, p.err, st)) return rc;
         add_split_kernel<<<g16, b16, 0, st>>>(vthi, vtlo, w.T1, w.Kt, n, ld, VEt_hi, VEt_lo, w.ew.VThi, w.ew.VTlo,
