@@ -74,6 +74,7 @@ struct GemmShape {
                             // returns at once (written by an earlier kernel on the same stream)
     unsigned *ticket;       // nullptr, or a zeroed counter: the last CTA to finish runs epi.tail()
     unsigned *err;          // device error word
+    int prof_as;            // profiling class + 1 for the launch timing (0: by precision)
 };
 
 // First tile column of row ti that reaches the upper triangle.
@@ -508,7 +509,7 @@ cudaError_t launch_gemm(const MatView *a16, const MatView *b16, const MatView *a
     if (prof) {
         // algorithmic flops: 2 M N K per matrix (M (M + 1) K for the symmetric Gram)
         const double f = shp.sym ? (double)shp.M * (shp.M + 1) * shp.K : 2.0 * shp.M * shp.N * (double)shp.K;
-        prof_end(st, f * batch, shp.prec ? -1 : shp.prec_uniform);
+        prof_end(st, f * batch, shp.prof_as > 0 ? shp.prof_as - 1 : (shp.prec ? -1 : shp.prec_uniform));
     }
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) cuda_fail(le, __FILE__, __LINE__);

@@ -559,6 +559,7 @@ static int gemm3p(const float *ahi, const float *alo, int M, int K, long long ld
     GemmShape s;
     memset(&s, 0, sizeof(s));
     s.M = M; s.N = N; s.K = K; s.prec_uniform = PREC_TF32X3; s.prec = prec; s.err = err;
+    s.prof_as = PREC_TF32X3 + 1;   // timed with the split-TF32 products (the per-matrix class is the polar chain)
     return launch_gemm(nullptr, nullptr, &vah, &val, &vbh, &vbl, s, B, e, st) == cudaSuccess ? PSVD_OK : PSVD_ERR_CUDA;
 }
 
