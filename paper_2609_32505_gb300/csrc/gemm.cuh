@@ -481,6 +481,16 @@ cudaError_t launch_gemm(const MatView *a16, const MatView *b16, const MatView *a
         if (e != cudaSuccess) { cuda_fail(e, __FILE__, __LINE__); return e; }
     }
     shp.bn = shp.N > 128 ? 256 : 128;
+    if (shp.bn == 256) {
+        // A launch with fewer 256-wide tiles than half the SMs is bound by one tile's serial
+        // k-loop (and, for split-TF32, its per-k-block flushes): 128-wide tiles put twice
+        // as many CTAs to work on it.
+        GemmShape t = shp;
+        t.tiles_m = (t.M + kBM - 1) / kBM;
+        t.tiles_n = (t.N + 255) / 256;
+        const long long tiles = (long long)host_tiles_per_matrix(t) * (shp.ksplit > 1 ? shp.ksplit : 1) * batch;
+        if (2 * tiles <= num_sms()) shp.bn = 128;
+    }
     GemmMaps maps;
     memset(&maps, 0, sizeof(maps));
     // Any map that is not supplied aliases a supplied one of the same role; the
