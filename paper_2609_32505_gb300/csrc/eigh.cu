@@ -4,9 +4,10 @@
 //     is left un-updated and corrected on the fly, so the rank-2 update of step k and
 //     the matrix-vector product of step k+1 touch only rows owned by the same warp).
 //  2. Eigenvalues of T by Sturm-count multisection (FP32, on T scaled to unit norm);
-//     eigenvalues with close neighbours refined by FP64 multisection.
-//  3. Eigenvectors of T by inverse iteration (FP64, one thread per eigenvalue,
-//     partially pivoted tridiagonal LU, operands streamed through shared memory),
+//     eigenvalues with close neighbours refined by multisection with float-float counts.
+//  3. Eigenvectors of T by inverse iteration (one thread per eigenvalue, partially
+//     pivoted tridiagonal LU, operands streamed through shared memory; float-float
+//     recurrences where a warp's eigenvalues are well separated, FP64 otherwise),
 //     Rayleigh quotients, modified Gram-Schmidt inside clusters of close eigenvalues.
 //  4. Back-transform V^T = Z^T Q^T with compact-WY blocks of kWY reflectors on the
 //     tcgen05 split-TF32 product kernel, then the sign convention (largest-|.| entry
@@ -406,7 +407,7 @@ __global__ void tri_bisect_kernel(const double *D, const double *E, int n, doubl
     lam[(long long)b * n + i] = 0.5 * ((double)lo + (double)hi) * tn;
 }
 
-// ------------------------------------------------------------ refinement (FP64)
+// ------------------------------------------------------------ refinement (float-float)
 // Float-float quotient a / b (a, b two-float values, b.hi != 0): the FP32 quotient of the
 // leading words, then one correction from the exact residual a - r b, so that the result
 // carries ~2^-44 relative accuracy on the FP32 pipe.
