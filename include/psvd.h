@@ -169,8 +169,8 @@ int psvd_polar_fwd(const float *A, float *W, float *H, int64_t batch, int64_t m,
  *   library until the process exits.  A problem whose psvd_polar_workspace_bytes exceeds
  *   it is rejected with PSVD_ERR_WORKSPACE before any work (psvd_last_error gives the
  *   needed and available bytes).  The first call on each device (and the first after a
- *   cudaDeviceReset) looks up the array's device address with that device current; make
- *   it before any stream capture.  Every call shares the one array and leaves its
+ *   cudaDeviceReset) looks up the array's device address with that device current.
+ *   Every call shares the one array and leaves its
  *   contents behind (each call clears what it needs), so calls that overlap on the GPU
  *   -- other streams, other host threads -- race; serialize them.  Calls no
  *   cudaMalloc/cudaFree and no allocating library routine. */
