@@ -142,6 +142,24 @@ def test_mixed_keeps_large_well_conditioned_result():
     assert O.ortho_error(u) <= 1e-4 and O.ortho_error(vt.T) <= 1e-4
 
 
+def test_mixed_batch_of_different_spectra():
+    # one batch, three condition numbers: the correction's first-order products drop to TF32
+    # matrix by matrix (when 2^-11 max|K| / (2 s_min) and 2^-11 max|X| stay below FP32
+    # resolution), so the matrices of one launch take different precisions; each must meet
+    # the gates on its own and agree with the plain path's singular values
+    n = 512
+    a = np.stack([W.constructed(30 + i, n, n, W.kappa_spectrum(n, k))[0]
+                  for i, k in enumerate((10.0, 1e2, 1e3))]).astype(np.float32).astype(np.float64)
+    u, s, vt, info = _svd(a, precision=1)
+    _, s_plain, _, _ = _svd(a, precision=0)
+    _fallback_consistent(info)
+    for b in range(3):
+        s_ref = O.svd(a[b])[1]
+        _gates(a[b], u[b], s[b], vt[b], s_ref, 1)
+        assert np.abs(s[b] - s_plain[b]).max() <= 1e-5 * s_ref[0]
+    assert info[0]["steps_tf32"] > 0 and info[0]["prec_fallback"] == 0
+
+
 def test_mixed_reconstruction_check_on_tall_input():
     # m > n: the low-precision steps tilt the column space of W; the probe estimate of the
     # reconstruction error sees it, and the result still meets the gates
