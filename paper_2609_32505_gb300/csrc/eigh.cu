@@ -1187,31 +1187,29 @@ __global__ void __launch_bounds__(kWY) s_times_tt_kernel(const float *S, int ks,
 // with S_a = M Y_a and S_b' = M Y_b from one product (S: columns [0, kWY) block b, [kWY, 2 kWY)
 // block a, the sum of ks K-split slices) and G_ab = Y_a^T Y_b.  S2 gets the same column order.
 // One block of 2 kWY threads per kPrRows rows (each thread one column of half the rows):
-// T_a, T_b and G_ab^T staged in shared memory with rows padded to kPrLd floats, so that a
-// thread reads 4 consecutive entries of its row as one float4 and the rows of S as float4
-// broadcasts.  T is upper triangular and zero past its block's width, and S is zeroed past
-// the pair's width, so the sums run over whole float4s.
-constexpr int kPrRows = 16, kPrLd = kWY + 4;
+// T_a and G_ab^T staged in shared memory with rows padded to kPrLd floats, so that a thread
+// reads 4 consecutive entries of its row as one float4 and the rows of S as float4
+// broadcasts; T_b replaces T_a once the first phase is done.  With two matrices resident,
+// 28 rows per block fit, so n = 4096 takes 147 blocks: one wave on the SMs.  T is upper
+// triangular and zero past its block's width, and S is zeroed past the pair's width, so
+// the sums run over whole float4s.
+constexpr int kPrRows = 28, kPrLd = kWY + 4;
+static_assert(kPrRows % 2 == 0, "two halves of the rows");
 constexpr size_t kPrSmem =
-    sizeof(float) * (3 * (size_t)kWY * kPrLd + (size_t)kPrRows * 2 * kWY + (size_t)kPrRows * kWY);
+    sizeof(float) * (2 * (size_t)kWY * kPrLd + (size_t)kPrRows * 2 * kWY + (size_t)kPrRows * kWY);
 __global__ void __launch_bounds__(2 * kWY) s_pair_kernel(const float *S, int ks, int B, const float *Tm,
                                                           const float *Gab, int n, int nblk, int npair, int blk_b,
                                                           int q, int nb_a, float *S2hi, float *S2lo) {
     extern __shared__ __align__(16) float psm[];
-    float *Ta = psm, *Tb = Ta + kWY * kPrLd, *Gt = Tb + kWY * kPrLd;
+    float *Ta = psm, *Gt = Ta + kWY * kPrLd, *Tb = Ta;  // T_b is loaded over T_a after phase one
     float *sr = Gt + kWY * kPrLd;                     // [kPrRows][2 kWY]: S rows, then S_b in place
     float *s2a = sr + kPrRows * 2 * kWY;              // [kPrRows][kWY]
     const int i0 = blockIdx.x * kPrRows, b = blockIdx.y, t = threadIdx.x;
     const int W = kWY + nb_a;
-    // the three kWY x kWY matrices (16-byte aligned rows) as float4 loads, eight in flight;
-    // G_ab is stored transposed (row j of Gt = column j of G_ab)
-#pragma unroll
-    for (int mtx = 0; mtx < 3; ++mtx) {
-        const float *src = mtx == 0 ? Tm + ((long long)b * nblk + blk_b + 1) * kWY * kWY
-                         : mtx == 1 ? Tm + ((long long)b * nblk + blk_b) * kWY * kWY
-                                    : Gab + ((long long)b * npair + q) * kWY * kWY;
+    // a kWY x kWY matrix (16-byte aligned rows) as float4 loads, eight in flight, into rows
+    // padded to kPrLd; G_ab is stored transposed (row j of Gt = column j of G_ab)
+    auto stage = [&](const float *src, float *dst, bool transposed) {
         const float4 *g4 = reinterpret_cast<const float4 *>(src);
-        float *dst = psm + mtx * kWY * kPrLd;
         for (int q0 = t; q0 < kWY * kWY / 4; q0 += 8 * 2 * kWY) {
             float4 v[8];
 #pragma unroll
@@ -1223,7 +1221,7 @@ __global__ void __launch_bounds__(2 * kWY) s_pair_kernel(const float *S, int ks,
                 if (e >= kWY * kWY) break;
                 const int r = e / kWY, c = e % kWY;
                 const float x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-                if (mtx < 2) {
+                if (!transposed) {
 #pragma unroll
                     for (int h = 0; h < 4; ++h) dst[r * kPrLd + c + h] = x[h];
                 } else {
@@ -1232,7 +1230,9 @@ __global__ void __launch_bounds__(2 * kWY) s_pair_kernel(const float *S, int ks,
                 }
             }
         }
-    }
+    };
+    stage(Tm + ((long long)b * nblk + blk_b + 1) * kWY * kWY, Ta, false);
+    stage(Gab + ((long long)b * npair + q) * kWY * kWY, Gt, true);
     const long long slice = (long long)B * n * 2 * kWY;
 #pragma unroll
     for (int r = 0; r < kPrRows; ++r) {
@@ -1266,7 +1266,8 @@ __global__ void __launch_bounds__(2 * kWY) s_pair_kernel(const float *S, int ks,
     }
 #pragma unroll
     for (int r = 0; r < kH; ++r) s2a[(rh + r) * kWY + j] = acc[r];
-    __syncthreads();
+    __syncthreads();                                 // T_a is no longer read: T_b takes its place
+    stage(Tm + ((long long)b * nblk + blk_b) * kWY * kWY, Tb, false);
 #pragma unroll
     for (int r = 0; r < kH; ++r) acc[r] = sr[(rh + r) * 2 * kWY + j];
     for (int l = 0; l < na4; l += 4) {               // S_b = S_b' - S2_a G_ab
